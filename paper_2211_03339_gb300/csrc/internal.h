@@ -1,0 +1,152 @@
+// internal.h -- host-side declarations shared by the translation units of
+// libmpjacobi.so.  Not part of the public ABI (see include/mpjacobi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/mpjacobi.h"
+
+namespace mpj {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* where, cudaError_t e);
+void set_error_msg(const char* msg);
+
+#define MPJ_CUDA_TRY(expr)                                                    \
+    do {                                                                      \
+        cudaError_t _e = (expr);                                              \
+        if (_e != cudaSuccess) { ::mpj::set_error(#expr, _e); return MPJ_CUDA_ERROR; } \
+    } while (0)
+
+#define MPJ_LAUNCH_CHECK(name)                                                \
+    do {                                                                      \
+        cudaError_t _e = cudaGetLastError();                                  \
+        if (_e != cudaSuccess) { ::mpj::set_error(name, _e); return MPJ_CUDA_ERROR; } \
+    } while (0)
+
+#define MPJ_TRY(expr)                                                         \
+    do { int _s = (expr); if (_s != MPJ_SUCCESS) return _s; } while (0)
+
+// ---------------------------------------------------------------- workspace
+// A bump allocator over one device buffer; every carve is 256-byte aligned.
+struct Arena {
+    char*  base = nullptr;
+    size_t size = 0;
+    size_t used = 0;
+    template <class T>
+    T* take(size_t count) {
+        size_t off = (used + 255) & ~size_t(255);
+        size_t bytes = count * sizeof(T);
+        if (base == nullptr) { used = off + bytes; return nullptr; }   // sizing pass
+        if (off + bytes > size) return nullptr;
+        used = off + bytes;
+        return reinterpret_cast<T*>(base + off);
+    }
+};
+
+// Owns a workspace: either the caller's buffer or a stream-ordered allocation.
+struct Workspace {
+    void*        ptr = nullptr;
+    bool         owned = false;
+    cudaStream_t stream = nullptr;
+    int acquire(void* caller, size_t caller_bytes, size_t need, cudaStream_t s);
+    ~Workspace();
+};
+
+// Pinned host scratch for the per-sweep convergence read-back.
+struct HostScratch {
+    double*             d = nullptr;
+    unsigned long long* u = nullptr;
+    int init();
+    ~HostScratch();
+};
+
+// ---------------------------------------------------------------- profiling
+// Kernel classes counted (and, when enabled, timed with CUDA events on the
+// launching stream) by ProfScope; names in prof.cu.
+enum ProfClass {
+    PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
+    PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
+    PC_APPLY1_F64, PC_AUX, kProfClasses
+};
+struct ProfScope {
+    int cls;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    ProfScope(int cls, cudaStream_t s);
+    ~ProfScope();
+};
+void prof_flush();
+#define MPJ_PROF(cls, stream) ::mpj::ProfScope _mpj_prof_scope((cls), (stream))
+
+// ---------------------------------------------------------------- shapes
+inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
+int choose_block(int n, const mpj_options* o);
+
+// ---------------------------------------------------------------- engines
+// Two-sided block Jacobi (Alg. 3.2 / step 4 of Alg. 4.1, parallel round-robin
+// block order) on a padded N x N symmetric matrix T (ld = N) and V (ld = N).
+struct SweepResult {
+    int    sweeps = 0;
+    double rotations = 0;       // applied (non-skipped) rotations, absolute count
+    double off_initial = 0;
+    double off_final = 0;
+    int    status = MPJ_SUCCESS;
+};
+
+template <class Real>
+size_t twosided_workspace_bytes(int N, int B);
+template <class Real>
+int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, double eps_skip,
+                    int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res);
+
+// One-sided block Jacobi (Alg. 5.1 / steps 4-10 of Alg. 5.2) on C (m x N, ld = ldc)
+// and V (N x N, ld = N).
+template <class Real>
+size_t onesided_workspace_bytes(int m, int N, int B);
+template <class Real>
+int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, double tol_rot,
+                    double ju_ratio, int max_sweeps, int max_inner, void* work, cudaStream_t s,
+                    SweepResult* res);
+
+// FP64 GEMM: C = alpha * op(A) * op(B) + beta * C (column-major).  When
+// upper_mirror is set, only tiles on or above the diagonal of the (square) C
+// are computed and each result is also written to the mirrored position.
+int dgemm(bool transA, bool transB, int M, int N, int K, double alpha, const double* A, int lda,
+          const double* B, int ldb, double beta, double* C, int ldc, bool upper_mirror,
+          cudaStream_t s);
+
+// Blocked MGS (Lemma 2.1) in place on Q (m x n, ld = ldq).  Needs n x 32 doubles
+// of workspace for the panel projections.
+size_t mgs_workspace_bytes(int m, int n);
+int mgs_inplace(double* Q, int m, int n, int ldq, void* work, int* d_flag, cudaStream_t s);
+
+// ---------------------------------------------------------------- helpers (kernels.cu)
+int copy_pad_f64(const double* A, int lda, int rows, int cols, double* T, int ldt, int Rpad,
+                 int Cpad, bool identity_pad, cudaStream_t s);
+int copy_pad_f32(const double* A, int lda, int rows, int cols, float* T, int ldt, int Rpad,
+                 int Cpad, bool identity_pad, cudaStream_t s);
+int set_identity_f64(double* V, int ld, int rows, int cols, cudaStream_t s);
+int set_identity_f32(float* V, int ld, int rows, int cols, cudaStream_t s);
+int copy_f64(const double* src, int lds, int rows, int cols, double* dst, int ldd, cudaStream_t s);
+int sumsq_f64(const double* A, int lda, int rows, int cols, double* partial, double* out,
+              cudaStream_t s);
+int offnorm2(const void* T, bool is_double, int ld, int n, double* partial, double* out,
+             cudaStream_t s);
+// ranks of keys (ascending or descending), ties broken by index; perm[rank] = i
+int rank_sort(const double* keys, int stride, int n, bool descending, int* perm, cudaStream_t s);
+int gather_vec(const double* in, const int* perm, int n, double* out, cudaStream_t s);
+int diag_to_f64(const void* T, bool is_double, int ld, int n, double* d, cudaStream_t s);
+int gather_eig(const double* T, int ldt, const double* Vw, int ldvw, const int* perm, int n,
+               double* Lambda, double* V, int ldv, cudaStream_t s);
+int gather_z32(const float* V32, int ld32, const int* perm, int n, double* Z, int ldz,
+               cudaStream_t s);
+int colnorms_f64(const double* C, int ldc, int m, int n, double* nrm, cudaStream_t s);
+int colnorms2_f32(const float* C, int ldc, int m, int n, double* nrm2, cudaStream_t s);
+int svd_post(const double* C, int ldc, const double* Vw, int ldvw, const double* nrm,
+             const int* perm, int m, int n, double* Sigma, double* U, int ldu, double* V,
+             int ldv, int* d_flag, cudaStream_t s);
+
+}  // namespace mpj

@@ -1,0 +1,248 @@
+// jacobi_device.cuh -- device building blocks of the block Jacobi engines.
+//
+//   rr_index        parallel (round-robin tournament) ordering: in round r the
+//                   2K blocks are paired so that every pair meets once in 2K-1
+//                   rounds; pairs of one round are disjoint (the GPU analogue of
+//                   the "merry-go-round" order of Sec. 6).
+//   rotation_cs     Lemma 3.1 (and, on a Gram matrix, Lemma 5.1).
+//   inner_jacobi    cyclic Jacobi on one 2b x 2b block-pair problem held in
+//                   shared memory, parallel order inside the block, with the
+//                   rotations accumulated into the orthogonal 2b x 2b block W.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace mpj {
+
+constexpr int kThreads = 256;
+
+// Player at position `pos` (0 <= pos < P, P even) in round r of the circle method:
+// position 0 holds player 0, the others rotate through players 1..P-1.
+__device__ __forceinline__ int rr_index(int r, int pos, int P) {
+    return pos == 0 ? 0 : 1 + (pos - 1 + r) % (P - 1);
+}
+
+// Lemma 3.1: (c, s) with mu = (a_qq - a_pp)/(2 a_pq), t = sign(mu)/(|mu| + sqrt(1+mu^2)),
+// c = 1/sqrt(1+t^2), s = t c.
+template <class Real>
+__device__ __forceinline__ void rotation_cs(Real app, Real aqq, Real apq, Real& c, Real& s, Real& t) {
+    Real mu = (aqq - app) / (Real(2) * apq);
+    Real am = mu < Real(0) ? -mu : mu;
+    t = Real(1) / (am + sqrt(Real(1) + mu * mu));
+    if (mu < Real(0)) t = -t;
+    c = Real(1) / sqrt(Real(1) + t * t);
+    s = t * c;
+}
+
+template <class Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
+
+// Shared-memory footprint of a block-pair solve for M = 2b: S, F and a third
+// M x (M+1) buffer (the Gram/correction matrix of the re-orthogonalisation),
+// c, s, c-1 of the M/2 rotations of a round, and pair indices / flags.
+template <class Real, int M>
+struct InnerLayout {
+    static constexpr int LD = M + 1;
+    static constexpr size_t bytes =
+        sizeof(Real) * (3 * M * LD + 4 * (M / 2)) + sizeof(int) * (3 * (M / 2) + 8);
+};
+
+// Cyclic Jacobi on the symmetric M x M matrix S (shared, column-major, ld M+1).
+// The accumulated rotation W = J_1 J_2 ... is kept as F = W - I (F must hold
+// the start, e.g. 0): F <- F J + (J - I), so that the rounding errors of F are
+// relative to |F| and W = I + F stays orthogonal to working precision when
+// the rotations are small (the nearly diagonal T of step 4 of Alg. 4.1).
+// One inner sweep = M-1 parallel rounds of M/2 disjoint rotations.  A pair is
+// skipped (its entry set to zero, not counted) when |s_pq| <= eps sqrt(|s_pp s_qq|)
+// (Remark 3.7) or |s_pq| <= tau (entries that cannot matter for the stopping
+// test).  Stops after an inner sweep with no rotation or after max_inner
+// sweeps.  Returns the number of rotations applied (all threads).
+// Must be called by all kThreads threads of the block.
+template <class Real, int M>
+__device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real tau, int max_inner) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    static_assert(P <= 32, "pair count must fit one warp");
+    Real* sn = cs + P;
+    Real* cm = sn + P;               // c - 1 = -s^2 / (1 + c)
+    Real* tt = cm + P;               // t = s / c
+    int* iq = ip + P;
+    int* sk = iq + P;
+    volatile int* cnt = sk + P;      // [0] applied in this sweep
+    const int tid = threadIdx.x;
+    int total = 0;
+    for (int sweep = 0; sweep < max_inner; ++sweep) {
+        int applied = 0;
+        for (int r = 0; r < M - 1; ++r) {
+            if (tid < 32) {
+                int mine = 0;
+                if (tid < P) {
+                    int p = rr_index(r, tid, M), q = rr_index(r, M - 1 - tid, M);
+                    if (p > q) { int t = p; p = q; q = t; }
+                    Real apq = S[q * LD + p], app = S[p * LD + p], aqq = S[q * LD + q];
+                    Real c = Real(1), s = Real(0), t = Real(0);
+                    int skip = 1;
+                    Real aa = rabs(apq);
+                    if (apq != Real(0) && aa > tau && !(aa <= eps * sqrt(rabs(app * aqq)))) {
+                        rotation_cs(app, aqq, apq, c, s, t);
+                        skip = 0;
+                    }
+                    cs[tid] = c; sn[tid] = s; cm[tid] = -(s * s) / (Real(1) + c); tt[tid] = t;
+                    ip[tid] = p; iq[tid] = q; sk[tid] = skip;
+                    mine = !skip;
+                }
+                applied += __popc(__ballot_sync(0xffffffffu, mine));
+            }
+            __syncthreads();
+            // two-sided update of the 2x2 blocks (a, b), a <= b, mirrored below the diagonal
+            for (int t = tid; t < P * P; t += kThreads) {
+                int a = t / P, b = t % P;
+                if (a > b) continue;
+                int pa = ip[a], qa = iq[a];
+                Real ca = cs[a], sa = sn[a];
+                if (a == b) {
+                    // b_pp = c^2 a_pp - 2 s c a_pq + s^2 a_qq and b_qq = s^2 a_pp + 2 s c a_pq
+                    // + c^2 a_qq reduce, for the (c, s) of Lemma 3.1, to a_pp - t a_pq and
+                    // a_qq + t a_pq: one rounding of a small correction instead of three
+                    // rounded products of the full diagonal entries.
+                    Real apq = S[qa * LD + pa], ta = tt[a];
+                    S[pa * LD + pa] = S[pa * LD + pa] - ta * apq;
+                    S[qa * LD + qa] = S[qa * LD + qa] + ta * apq;
+                    S[qa * LD + pa] = Real(0);
+                    S[pa * LD + qa] = Real(0);
+                } else {
+                    if (sk[a] && sk[b]) continue;     // both rotations are the identity
+                    int pb = ip[b], qb = iq[b];
+                    Real cb = cs[b], sb = sn[b];
+                    Real x00 = S[pb * LD + pa], x01 = S[qb * LD + pa];
+                    Real x10 = S[pb * LD + qa], x11 = S[qb * LD + qa];
+                    // rows: J_a^T X
+                    Real y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+                    Real y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+                    // columns: (J_a^T X) J_b
+                    Real z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
+                    Real z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
+                    S[pb * LD + pa] = z00; S[qb * LD + pa] = z01;
+                    S[pb * LD + qa] = z10; S[qb * LD + qa] = z11;
+                    S[pa * LD + pb] = z00; S[pa * LD + qb] = z01;
+                    S[qa * LD + pb] = z10; S[qa * LD + qb] = z11;
+                }
+            }
+            // F <- F J + (J - I): columns p, q of every rotation
+            for (int t = tid; t < M * P; t += kThreads) {
+                int row = t % M, a = t / M;
+                if (sk[a]) continue;
+                int pa = ip[a], qa = iq[a];
+                Real c = cs[a], s = sn[a];
+                Real fp = F[pa * LD + row], fq = F[qa * LD + row];
+                Real np = c * fp - s * fq, nq = s * fp + c * fq;
+                if (row == pa) { np += cm[a]; nq += s; }
+                else if (row == qa) { np -= s; nq += cm[a]; }
+                F[pa * LD + row] = np;
+                F[qa * LD + row] = nq;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) cnt[0] = applied;
+        __syncthreads();
+        int c = cnt[0];
+        __syncthreads();
+        total += c;
+        if (c == 0) break;
+    }
+    return total;
+}
+
+// One Newton-Schulz step towards the orthogonal polar factor of W = I + F:
+// G = W^T W - I = F + F^T + F^T F,  W <- W (I - G/2), i.e.
+// F <- F - G/2 - F G/2.  G is the scratch buffer (ld M+1).  Used when the
+// block rotation is far from the identity, where the M-1 rounds of rotations
+// leave W non-orthogonal by a few hundred ulps.
+template <class Real, int M>
+__device__ void reorthogonalise(Real* F, Real* G) {
+    constexpr int LD = M + 1;
+    constexpr int RM = M / 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    Real acc[RM][RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) acc[i][j] = Real(0);
+    for (int k = 0; k < M; ++k) {
+        Real a[RM], b[RM];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = F[(ty * RM + i) * LD + k];   // F[k][R]
+#pragma unroll
+        for (int j = 0; j < RM; ++j) b[j] = F[(tx * RM + j) * LD + k];   // F[k][C]
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) {
+            int R = ty * RM + i, C = tx * RM + j;
+            G[C * LD + R] = (F[C * LD + R] + F[R * LD + C]) + acc[i][j];
+        }
+    __syncthreads();
+    // acc = (F G)[R][C]
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) acc[i][j] = Real(0);
+    for (int k = 0; k < M; ++k) {
+        Real a[RM], b[RM];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) a[i] = F[k * LD + ty * RM + i];     // F[R][k]
+#pragma unroll
+        for (int j = 0; j < RM; ++j) b[j] = G[(tx * RM + j) * LD + k];   // G[k][C]
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) {
+            int R = ty * RM + i, C = tx * RM + j;
+            F[C * LD + R] = F[C * LD + R] - Real(0.5) * (G[C * LD + R] + acc[i][j]);
+        }
+    __syncthreads();
+}
+
+// Block solve epilogue shared by the two engines: optionally re-orthogonalise
+// W = I + F (when max |F| >= gate), then store F row-major to Fout.
+template <class Real, int M>
+__device__ void finish_block(Real* F, Real* G, Real* Fout, Real gate, int* flag) {
+    constexpr int LD = M + 1;
+    if (threadIdx.x == 0) flag[0] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+        int r = t % M, c = t / M;
+        if (rabs(F[c * LD + r]) >= gate) flag[0] = 1;
+    }
+    __syncthreads();
+    if (flag[0]) reorthogonalise<Real, M>(F, G);
+    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+        int k = t / M, c = t % M;
+        Fout[t] = F[c * LD + k];                 // row-major: Fout[k*M + c] = F[k][c]
+    }
+}
+
+// Local index l in [0, 2b) of the block pair (I, J) -> global row/column index.
+__device__ __forceinline__ int pair_global(int l, int I, int J, int b) {
+    return l < b ? I * b + l : J * b + (l - b);
+}
+
+// Block pair handled by CTA `pair` in round `round` (2K = number of blocks).
+__device__ __forceinline__ void round_pair(int round, int pair, int nblocks, int& I, int& J) {
+    I = rr_index(round, pair, nblocks);
+    J = rr_index(round, nblocks - 1 - pair, nblocks);
+    if (I > J) { int t = I; I = J; J = t; }
+}
+
+}  // namespace mpj

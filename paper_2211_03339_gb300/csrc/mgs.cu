@@ -1,0 +1,183 @@
+// mgs.cu -- blocked modified Gram-Schmidt (Lemma 2.1; step 2 of Alg. 4.1/5.2).
+//
+// The columns are processed in panels of 32.  A panel is orthogonalised by
+// classic column-by-column MGS:
+//     r_jj = ||w_j||,  q_j = w_j / r_jj,  w_k = w_k - (q_j^T w_k) q_j  (k > j in panel)
+// by ONE thread-block cluster of 8 CTAs that splits the m rows between its
+// CTAs.  For each column the CTAs form partial inner products w_j^T w_k over
+// their rows, exchange them through distributed shared memory (one cluster
+// barrier per column, double-buffered), sum them in a fixed order, and update
+// their rows.  Rows are read with consecutive threads on consecutive rows
+// (coalesced, column-major).  The trailing columns then receive the panel's
+// projections, W = W - Q_p (Q_p^T W), as two FP64 GEMMs (block MGS).
+#include <cooperative_groups.h>
+#include <cmath>
+
+#include "internal.h"
+#include "jacobi_device.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace mpj {
+
+constexpr int PB = 32;        // panel width
+constexpr int CL = 8;         // CTAs per cluster (portable size)
+
+__global__ void __cluster_dims__(CL, 1, 1) __launch_bounds__(kThreads)
+k_mgs_panel(double* __restrict__ Q, int m, int ldq, int j0, int pb, int* __restrict__ flag) {
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    __shared__ double part[2][PB];      // this CTA's partial inner products
+    __shared__ double red[PB];          // warp partials folded per column
+    const int rows_per = (m + CL - 1) / CL;
+    const int r0 = rank * rows_per;
+    const int r1 = min(m, r0 + rows_per);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = kThreads / 32;
+    double* P = Q + (size_t)j0 * ldq;
+    for (int jj = 0; jj < pb; ++jj) {
+        const int buf = jj & 1;
+        const double* wj = P + (size_t)jj * ldq;
+        // partial g_k = sum_rows w_j * w_k for k = jj..pb-1: warp w takes k = jj+w, jj+w+NW, ...
+        for (int k = jj + warp; k < pb; k += NW) {
+            const double* wk = P + (size_t)k * ldq;
+            double sacc = 0.0;
+            for (int r = r0 + lane; r < r1; r += 32) sacc = fma(wj[r], wk[r], sacc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) part[buf][k] = sacc;
+        }
+        cluster.sync();                 // partials of this column visible cluster-wide
+        if (threadIdx.x < PB) {
+            int k = threadIdx.x;
+            double g = 0.0;
+            if (k >= jj && k < pb) {
+                for (int c = 0; c < CL; ++c) {
+                    double* remote = cluster.map_shared_rank(&part[buf][0], c);
+                    g += remote[k];
+                }
+            }
+            red[k] = g;
+        }
+        __syncthreads();
+        const double rjj = sqrt(red[jj]);
+        if (rjj == 0.0 || !(rjj == rjj)) {
+            if (threadIdx.x == 0 && rank == 0) atomicExch(flag, 1);
+        }
+        const double inv = (rjj > 0.0) ? 1.0 / rjj : 0.0;
+        // q_j = w_j / r_jj ; w_k -= (g_k / r_jj) q_j for k > jj
+        for (int r = r0 + threadIdx.x; r < r1; r += kThreads) {
+            double q = P[(size_t)jj * ldq + r] * inv;
+            P[(size_t)jj * ldq + r] = q;
+            for (int k = jj + 1; k < pb; ++k) {
+                double rk = red[k] * inv;
+                P[(size_t)k * ldq + r] = fma(-rk, q, P[(size_t)k * ldq + r]);
+            }
+        }
+        __syncthreads();                // own rows updated before the next column's dots
+    }
+    cluster.sync();                     // no CTA leaves while others may read its part[]
+}
+
+// Panel projections R = Q_p^T W (pb x rest, K = m rows): the contraction is
+// long and the output small, so the rows are split across CTAs (grid.y) and
+// the partial products are summed in a fixed order by k_proj_reduce.
+constexpr int KSPLIT_ROWS = 256;
+
+__global__ void __launch_bounds__(kThreads)
+k_proj_partial(const double* __restrict__ Qp, const double* __restrict__ Wr, int ldq, int m,
+               int pb, int rest, double* __restrict__ Rpart) {
+    __shared__ __align__(16) double Qs[16][PB + 1];     // Qs[row][j]
+    __shared__ __align__(16) double Ws[16][64 + 2];     // Ws[row][c]
+    const int c0 = blockIdx.x * 64;
+    const int r0 = blockIdx.y * KSPLIT_ROWS;
+    const int r1 = min(m, r0 + KSPLIT_ROWS);
+    // thread -> 2 rows (j) x 4 cols of the 32 x 64 partial
+    const int tj = threadIdx.x >> 4, tc = threadIdx.x & 15;
+    double acc[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};
+    for (int rc = r0; rc < r1; rc += 16) {
+        for (int t = threadIdx.x; t < 16 * PB; t += kThreads) {
+            int rr = t % 16, j = t / 16;
+            int gr = rc + rr;
+            Qs[rr][j] = (gr < r1 && j < pb) ? Qp[(size_t)gr + (size_t)j * ldq] : 0.0;
+        }
+        for (int t = threadIdx.x; t < 16 * 64; t += kThreads) {
+            int rr = t % 16, c = t / 16;
+            int gr = rc + rr, gc = c0 + c;
+            Ws[rr][c] = (gr < r1 && gc < rest) ? Wr[(size_t)gr + (size_t)gc * ldq] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int rr = 0; rr < 16; ++rr) {
+            double a0 = Qs[rr][tj * 2], a1 = Qs[rr][tj * 2 + 1];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                double b = Ws[rr][tc * 4 + k];
+                acc[0][k] = fma(a0, b, acc[0][k]);
+                acc[1][k] = fma(a1, b, acc[1][k]);
+            }
+        }
+        __syncthreads();
+    }
+    double* Rp = Rpart + (size_t)blockIdx.y * PB * rest;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            int j = tj * 2 + i, c = c0 + tc * 4 + k;
+            if (j < pb && c < rest) Rp[(size_t)c * PB + j] = acc[i][k];
+        }
+}
+
+__global__ void k_proj_reduce(const double* __restrict__ Rpart, int nsplit, int pb, int rest,
+                              double* __restrict__ R) {
+    size_t total = (size_t)PB * rest;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        int j = (int)(t % PB);
+        double v = 0.0;
+        if (j < pb)
+            for (int sp = 0; sp < nsplit; ++sp) v += Rpart[(size_t)sp * PB * rest + t];
+        R[t] = v;
+    }
+}
+
+static int ksplit_for(int m) { return (m + KSPLIT_ROWS - 1) / KSPLIT_ROWS; }
+
+size_t mgs_workspace_bytes(int m, int n) {
+    size_t nn = (size_t)(n > 0 ? n : 1);
+    return sizeof(double) * (size_t)PB * nn * (1 + (size_t)ksplit_for(m > 0 ? m : 1)) + 1024;
+}
+
+// In place: Q (m x n, ld ldq) <- orthonormal factor of the QR factorisation.
+int mgs_inplace(double* Q, int m, int n, int ldq, void* work, int* d_flag, cudaStream_t s) {
+    double* R = static_cast<double*>(work);      // PB x (n - j0 - pb) panel projections
+    double* Rpart = R + (size_t)PB * n;          // ksplit partials of R
+    const int ksplit = ksplit_for(m);
+    for (int j0 = 0; j0 < n; j0 += PB) {
+        int pb = (n - j0) < PB ? (n - j0) : PB;
+        { MPJ_PROF(PC_MGS_PANEL, s);
+    k_mgs_panel<<<CL, kThreads, 0, s>>>(Q, m, ldq, j0, pb, d_flag); }
+        MPJ_LAUNCH_CHECK("k_mgs_panel");
+        int rest = n - j0 - pb;
+        if (rest > 0) {
+            const double* Qp = Q + (size_t)j0 * ldq;
+            double* Wr = Q + (size_t)(j0 + pb) * ldq;
+            // R = Q_p^T W   (pb x rest), split over row slabs
+            dim3 g((rest + 63) / 64, ksplit);
+            { MPJ_PROF(PC_MGS_PROJ, s);
+    k_proj_partial<<<g, kThreads, 0, s>>>(Qp, Wr, ldq, m, pb, rest, Rpart); }
+            MPJ_LAUNCH_CHECK("k_proj_partial");
+            size_t tot = (size_t)PB * rest;
+            int rg = (int)((tot + kThreads - 1) / kThreads);
+            { MPJ_PROF(PC_MGS_PROJ, s);
+    k_proj_reduce<<<rg, kThreads, 0, s>>>(Rpart, ksplit, pb, rest, R); }
+            MPJ_LAUNCH_CHECK("k_proj_reduce");
+            // W = W - Q_p R
+            MPJ_TRY(dgemm(false, false, m, rest, pb, -1.0, Qp, ldq, R, PB, 1.0, Wr, ldq, false, s));
+        }
+    }
+    return MPJ_SUCCESS;
+}
+
+}  // namespace mpj

@@ -1,0 +1,246 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (binding, from the stated accuracy targets; u = 2^-53):
+  relative residual   ||A V - V Lambda||_F / ||A||_F   <= 10 n u
+  orthogonality       ||V^T V - I||_F                  <= 10 n u
+  eigenvalues         |lambda_i - lambda_i^oracle|     <= 10 n u ||A||_2
+The oracle runs at sizes it finishes in seconds (several 64-wide tiles plus a
+ragged tail); the full-size cases are checked through properties that hold at
+any size (residual, orthogonality, the constructed spectrum).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2211_03339_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+UPS = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def mpj():
+    if not torch.cuda.is_available():
+        pytest.fail("gpu tests selected but no CUDA device is visible")
+    from paper_2211_03339_gb300 import build
+    build.build()
+    import paper_2211_03339_gb300 as m
+    return m
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def evd_metrics(A, lam, V):
+    n = A.shape[0]
+    res = np.linalg.norm(A @ V - V * lam) / np.linalg.norm(A)
+    orth = np.linalg.norm(V.T @ V - np.eye(n))
+    return res, orth
+
+
+def sign_fix(V):
+    idx = np.argmax(np.abs(V), axis=0)
+    s = np.sign(V[idx, np.arange(V.shape[1])])
+    s[s == 0] = 1
+    return V * s
+
+
+# ------------------------------------------------------------------ single steps
+@pytest.mark.parametrize("n", [33, 64, 200, 300])
+def test_mgs_parity(mpj, n):
+    A, _ = synth.sym_matrix(n, "uniform", seed=100 + n)
+    Z, D, _ = oracle.stage1_syev_f(A)          # a nearly orthonormal Z, as in step 2
+    Qo, Ro, rc = oracle.mgs(Z)
+    assert rc == 0
+    Qg = host(mpj.mgs(dev(Z)))
+    assert np.abs(Qg - Qo).max() <= 10 * n * U
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(n)) <= 10 * n * U
+
+
+@pytest.mark.parametrize("m,n", [(40, 40), (130, 70), (257, 100)])
+def test_mgs_parity_general(mpj, m, n):
+    rng = np.random.default_rng(m + n)
+    Z = rng.standard_normal((m, n))
+    Qo, Ro, rc = oracle.mgs(Z)
+    kappa = np.linalg.cond(Z)
+    Qg = host(mpj.mgs(dev(Z)))
+    assert np.abs(Qg - Qo).max() <= 10 * n * U * kappa
+
+
+@pytest.mark.parametrize("n", [17, 64, 129, 300])
+def test_congruence_parity(mpj, n):
+    A, _ = synth.sym_matrix(n, "uniform", seed=200 + n)
+    Q = synth.haar(synth.rng_for(300 + n), n)
+    To = oracle.congruence(A, Q)
+    Tg = host(mpj.congruence(dev(A), dev(Q)))
+    assert np.array_equal(Tg, Tg.T)
+    gn = n * U / (1 - n * U)
+    bound = gn * (2 + gn) * (np.abs(Q).T @ np.abs(A) @ np.abs(Q))
+    assert (np.abs(Tg - To) <= 2 * bound).all()
+
+
+@pytest.mark.parametrize("n", [64, 200])
+def test_sweeps_parity(mpj, n):
+    A, lam = synth.sym_matrix(n, "uniform", seed=400 + n)
+    Lo, Vo, sto, rco, Qo, T0 = oracle.syevj_mp(A, intermediates=True)
+    normA = np.linalg.norm(A)
+    Tg, Pg, st = mpj.sweeps(dev(T0), dev(Qo), tol=n * U, normA=normA)
+    Tg, Pg = host(Tg), host(Pg)
+    lam_g = np.sort(np.diag(Tg))
+    a2 = np.abs(lam).max()
+    assert np.abs(lam_g - Lo).max() <= 10 * n * U * a2
+    assert oracle.offnorm(Tg) <= n * U * normA
+    assert 1 <= st["sweeps"] <= 6
+    res, orth = evd_metrics(A, np.diag(Tg), Pg)
+    assert res <= 10 * n * U and orth <= 10 * n * U
+
+
+@pytest.mark.parametrize("n", [64, 200])
+def test_stage1_fp32(mpj, n):
+    A, lam = synth.sym_matrix(n, "uniform", seed=500 + n)
+    Z, D, st = mpj.stage1_syevj32(dev(A))
+    Z, D = host(Z), host(D)
+    a2 = np.abs(lam).max()
+    assert (np.diff(D) >= 0).all()
+    # FP32 eigenvalues within single precision accuracy of the exact spectrum
+    assert np.abs(D - lam).max() <= 10 * n * UPS * a2
+    init_res = np.linalg.norm(A @ Z - Z * D) / np.linalg.norm(A)
+    assert init_res <= 10 * n * UPS
+    assert np.linalg.norm(Z.T @ Z - np.eye(n)) <= 10 * n * UPS
+    # Z is exactly representable in single precision (step 1 stores it at omega)
+    assert np.array_equal(Z, Z.astype(np.float32).astype(np.float64))
+
+
+# ------------------------------------------------------------------ end to end (EVD)
+@pytest.mark.parametrize("kind", ["uniform", "geometric", "cluster"])
+@pytest.mark.parametrize("n", [5, 64, 100, 257])
+@pytest.mark.parametrize("method", ["mp", "plain"])
+def test_syevj_parity(mpj, n, kind, method):
+    A, lam = synth.sym_matrix(n, kind, seed=synth.seed_for(1, n))
+    Lo, Vo, sto, rco = oracle.syevj_plain(A)
+    f = mpj.syevj_mp if method == "mp" else mpj.syevj_plain
+    Lg, Vg, st = f(dev(A))
+    Lg, Vg = host(Lg), host(Vg)
+    a2 = np.abs(lam).max()
+    assert np.abs(Lg - Lo).max() <= 10 * n * U * a2
+    res, orth = evd_metrics(A, Lg, Vg)
+    assert res <= 10 * n * U, res
+    assert orth <= 10 * n * U, orth
+    # eigenvectors of well separated eigenvalues agree with the oracle's up to sign
+    gaps = np.minimum(np.abs(np.diff(Lo, prepend=-np.inf)), np.abs(np.diff(Lo, append=np.inf)))
+    sep = gaps > 1e-3 * a2
+    if sep.any():
+        dv = np.abs(sign_fix(Vg)[:, sep] - sign_fix(Vo)[:, sep]).max(axis=0)
+        assert (dv <= 100 * n * U * a2 / gaps[sep]).all()
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_syevj_tiny(mpj, n):
+    A, lam = synth.sym_matrix(n, "uniform", seed=7 + n)
+    for f in (mpj.syevj_mp, mpj.syevj_plain):
+        Lg, Vg, st = f(dev(A))
+        Lg, Vg = host(Lg), host(Vg)
+        assert np.abs(Lg - np.sort(lam)).max() <= 64 * U
+        res, orth = evd_metrics(A, Lg, Vg)
+        assert res <= 64 * U and orth <= 64 * U
+
+
+def test_syevj_diagonal_and_zero(mpj):
+    n = 70
+    d = np.linspace(-3, 2, n)[::-1].copy()
+    A = np.diag(d)
+    for f in (mpj.syevj_mp, mpj.syevj_plain):
+        Lg, Vg, st = f(dev(A))
+        assert np.array_equal(host(Lg), np.sort(d))
+    Z = np.zeros((40, 40))
+    Lg, Vg, st = mpj.syevj_plain(dev(Z))
+    assert (host(Lg) == 0).all()
+    assert np.array_equal(host(Vg), np.eye(40))
+
+
+def test_syevj_nonfinite_input(mpj):
+    A, _ = synth.sym_matrix(32, "uniform", seed=1)
+    A[3, 5] = A[5, 3] = np.nan
+    with pytest.raises(mpj.MPJError) as e:
+        mpj.syevj_mp(dev(A))
+    assert e.value.status == 2
+
+
+def test_syevj_lda_larger_than_n(mpj):
+    import ctypes
+    n, lda = 50, 64
+    A, lam = synth.sym_matrix(n, "geometric", seed=3)
+    buf = np.zeros((lda, n), order="F"); buf[:n, :] = A
+    Ad = dev(buf.T)                              # row-major (n, lda) view = column-major lda x n
+    L = mpj.lib()
+    lamd = torch.empty(n, dtype=torch.float64, device="cuda")
+    Vd = torch.zeros((n, 72), dtype=torch.float64, device="cuda")   # ldv = 72
+    st = mpj.Stats()
+    rc = L.mpj_syevj_mp(ctypes.c_void_p(Ad.data_ptr()), n, lda, ctypes.c_void_p(lamd.data_ptr()),
+                        ctypes.c_void_p(Vd.data_ptr()), 72, n * U, None, ctypes.byref(st), None, 0,
+                        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 0
+    V = host(Vd).T[:n, :]
+    res, orth = evd_metrics(A, host(lamd), V)
+    assert res <= 10 * n * U and orth <= 10 * n * U
+    assert (host(Vd).T[n:, :] == 0).all()         # rows beyond n of the ldv slab untouched
+
+
+def test_not_converged_status(mpj):
+    A, lam = synth.sym_matrix(128, "uniform", seed=9)
+    Lg, Vg, st = mpj.syevj_plain(dev(A), options={"max_sweeps": 1, "max_inner": 1},
+                                 allow_not_converged=True)
+    assert st["status"] == 3 and st["sweeps"] == 1
+    with pytest.raises(mpj.MPJError):
+        mpj.syevj_plain(dev(A), options={"max_sweeps": 1, "max_inner": 1})
+
+
+# ------------------------------------------------------------------ full size, properties
+@pytest.mark.parametrize("n", [1024, 4096])
+def test_syevj_full_size_properties(mpj, n):
+    A, lam = synth.sym_matrix(n, "uniform", seed=synth.seed_for(1, n))
+    a2 = np.abs(lam).max()
+    for f in (mpj.syevj_mp, mpj.syevj_plain):
+        Lg, Vg, st = f(dev(A))
+        Lg, Vg = host(Lg), host(Vg)
+        res, orth = evd_metrics(A, Lg, Vg)
+        assert res <= 10 * n * U, (f.__name__, res)
+        assert orth <= 10 * n * U, (f.__name__, orth)
+        # constructed spectrum, with the slack of forming fl(Q diag(lam) Q^T)
+        assert np.abs(Lg - lam).max() <= 10 * n * U * a2 + 4 * n * U * a2
+
+
+# ------------------------------------------------------------------ SVD
+@pytest.mark.parametrize("m,n", [(48, 24), (200, 100), (300, 257)])
+@pytest.mark.parametrize("method", ["mp", "plain"])
+def test_gesvj_parity(mpj, m, n, method):
+    A, sig, Uc, Vc = synth.svd_matrix(m, n, seed=synth.seed_for(2, n), sigma_min=1e-10)
+    So, Uo, Vo, sto, rco = oracle.gesvj_plain(A)
+    f = mpj.gesvj_mp if method == "mp" else mpj.gesvj_plain
+    Sg, Ug, Vg, st = f(dev(A))
+    Sg, Ug, Vg = host(Sg), host(Ug), host(Vg)
+    assert (np.diff(Sg) <= 0).all()
+    assert np.abs(Sg - So).max() <= 10 * n * U * sig[0]
+    assert np.abs(Sg - sig).max() <= 10 * n * U * sig[0] + 4 * n * U * sig[0]
+    assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
+    assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
+    assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
+
+
+def test_gesvj_full_size_properties(mpj):
+    m, n = 4096, 2048
+    A, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, 0), sigma_min=1e-10)
+    Sg, Ug, Vg, st = mpj.gesvj_mp(dev(A))
+    Sg, Ug, Vg = host(Sg), host(Ug), host(Vg)
+    assert np.abs(Sg - sig).max() <= 10 * n * U * sig[0] + 4 * n * U * sig[0]
+    assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
+    assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
+    assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
