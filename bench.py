@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--spectrum", default="uniform")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--once", action="store_true",
+                    help="run one mpj_syevj_mp solve and exit (for profiler captures)")
     return ap.parse_args()
 
 
@@ -370,8 +372,23 @@ def run_ours(args):
     return 0
 
 
+def run_once(args):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import synth
+    A_np, _ = synth.sym_matrix(args.n, args.spectrum, seed=synth_seed(0))
+    L, V, st = mpj.syevj_mp(torch.from_numpy(A_np).cuda())
+    torch.cuda.synchronize()
+    print(json.dumps({"once": True, "n": args.n, "stats": st}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.once:
+        return run_once(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
