@@ -149,6 +149,29 @@ int mpj_mgs(const double* Z, int m, int n, int ldz, double* Q, int ldq,
             void* work, size_t work_bytes, void* stream);
 size_t mpj_mgs_workspace_bytes(int m, int n);
 
+/* mpj_mgs_noalloc -- the same blocked MGS as mpj_mgs for callers that cannot
+ * allocate device memory at call time: for instance code running where an
+ * allocation could block on a device-wide synchronisation or fail under memory
+ * pressure (a latency-critical loop), or applications whose own memory manager
+ * owns all device memory and does not allow allocations from libraries.  The
+ * paper has no counterpart: this is a service variant of Lemma 2.1's step.
+ *   Z, m, n, ldz, Q, ldq, stream: as for mpj_mgs.  Nothing is allocated and
+ *   nothing is freed (no cudaMalloc, cudaFree or allocating library routine).
+ *   Scratch: a fixed device array of MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES
+ *   doubles (8 MiB) compiled into the library; it is reserved on every GPU that
+ *   loads the library until the process exits.  A call needs
+ *   32 * n * (1 + ceil(m / 256)) doubles of it (square Z: up to n = 2048);
+ *   larger sizes are rejected with MPJ_BAD_ARG before any device work.
+ *   The first call on a device looks up the array's device address (a host-side
+ *   set-up step); make that first call before any stream capture.
+ *   All calls share the one array, which keeps the previous call's contents:
+ *   calls that may overlap on the GPU (different streams, or several host
+ *   threads) race on it and must be serialised by the caller.
+ *   Returns MPJ_RANK_DEFICIENT if some r_jj == 0; the call synchronises the
+ *   stream (it reads that flag). */
+#define MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES (1u << 20)
+int mpj_mgs_noalloc(const double* Z, int m, int n, int ldz, double* Q, int ldq, void* stream);
+
 /* Step 3 of Alg. 4.1: T = Q^T (A Q) in FP64 (A n x n symmetric, Q n x n).  The
  * upper triangle is computed and mirrored, so T is exactly symmetric. */
 int mpj_congruence(const double* A, int lda, const double* Q, int ldq, int n,

@@ -35,7 +35,7 @@ STATUS = {0: "success", 1: "invalid argument", 2: "input holds NaN or Inf",
 
 EXPORTS = ["mpj_syevj_mp", "mpj_syevj_plain", "mpj_syevj_workspace_bytes",
            "mpj_gesvj_mp", "mpj_gesvj_plain", "mpj_gesvj_workspace_bytes",
-           "mpj_stage1_syevj32", "mpj_mgs", "mpj_mgs_workspace_bytes",
+           "mpj_stage1_syevj32", "mpj_mgs", "mpj_mgs_workspace_bytes", "mpj_mgs_noalloc",
            "mpj_congruence", "mpj_congruence_workspace_bytes",
            "mpj_sweeps", "mpj_sweeps_workspace_bytes",
            "mpj_profile_enable", "mpj_profile_reset", "mpj_profile_read", "mpj_profile_name",
@@ -100,6 +100,7 @@ def lib():
         L.mpj_stage1_syevj32.restype = i
         L.mpj_mgs.argtypes = [p, i, i, i, p, i, p, sz, p]; L.mpj_mgs.restype = i
         L.mpj_mgs_workspace_bytes.argtypes = [i, i]; L.mpj_mgs_workspace_bytes.restype = sz
+        L.mpj_mgs_noalloc.argtypes = [p, i, i, i, p, i, p]; L.mpj_mgs_noalloc.restype = i
         L.mpj_congruence.argtypes = [p, i, p, i, i, p, i, p, sz, p]; L.mpj_congruence.restype = i
         L.mpj_congruence_workspace_bytes.argtypes = [i]
         L.mpj_congruence_workspace_bytes.restype = sz
@@ -244,6 +245,19 @@ def mgs(Z):
     ws = _workspace(lib().mpj_mgs_workspace_bytes(m, n), Z.device)
     rc = lib().mpj_mgs(_ptr(Zc), m, n, m, _ptr(Qc), m, _ptr(ws), ws.numel(), _stream_ptr(Z.device))
     _check(rc, "mpj_mgs")
+    return Qc.t()
+
+
+def mgs_noalloc(Z):
+    """mgs() without any device allocation: scratch comes from a fixed array in the
+    library (for callers that cannot allocate at call time; see include/mpjacobi.h
+    for the size limit and the rule that overlapping calls must be serialised)."""
+    torch = _torch()
+    m, n = Z.shape
+    Zc = _colmajor(Z)
+    Qc = torch.empty((n, m), dtype=torch.float64, device=Z.device)
+    rc = lib().mpj_mgs_noalloc(_ptr(Zc), m, n, m, _ptr(Qc), m, _stream_ptr(Z.device))
+    _check(rc, "mpj_mgs_noalloc")
     return Qc.t()
 
 

@@ -12,6 +12,7 @@
 // projections, W = W - Q_p (Q_p^T W), as two FP64 GEMMs (block MGS).
 #include <cooperative_groups.h>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 #include "jacobi_device.cuh"
@@ -180,4 +181,64 @@ int mgs_inplace(double* Q, int m, int n, int ldq, void* work, int* d_flag, cudaS
     return MPJ_SUCCESS;
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+// mpj_mgs_noalloc runs the same blocked MGS as mpj_mgs but takes its scratch
+// (the panel projections R and their split partials, plus the rank flag) from
+// a fixed array compiled into the library instead of allocating it.  The array
+// lives in device global memory on every GPU that loads the library, from load
+// until the process exits.  In host code g_mgs_noalloc_scratch is only a
+// host-side stand-in for the device array, so its device address is looked up
+// with cudaGetSymbolAddress (once per device) and passed to the kernels.
+static __device__ __align__(256) double g_mgs_noalloc_scratch[MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES + 32];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device; the first call on
+// a device performs the lookup.
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    MPJ_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) { set_error_msg("device ordinal out of range"); return MPJ_BAD_ARG; }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        MPJ_CUDA_TRY(cudaGetSymbolAddress(&p, g_mgs_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return MPJ_SUCCESS;
+}
+}  // namespace
+
+size_t mgs_noalloc_scratch_doubles(int m, int n) {
+    return (size_t)PB * (size_t)n * (1 + (size_t)ksplit_for(m));
+}
+
 }  // namespace mpj
+
+extern "C" int mpj_mgs_noalloc(const double* Z, int m, int n, int ldz, double* Q, int ldq,
+                               void* stream) {
+    using namespace mpj;
+    if (!Z || !Q || n < 1 || m < n || ldz < m || ldq < m) { set_error_msg("invalid argument"); return MPJ_BAD_ARG; }
+    if (mgs_noalloc_scratch_doubles(m, n) > (size_t)MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES) {
+        set_error_msg("mpj_mgs_noalloc: 32*n*(1+ceil(m/256)) doubles of scratch exceed "
+                      "MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES; use mpj_mgs with a workspace");
+        return MPJ_BAD_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double* scratch = nullptr;
+    MPJ_TRY(noalloc_scratch(&scratch));
+    int* flag = reinterpret_cast<int*>(scratch + MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES);
+    // the array keeps the previous call's contents: the rank flag must start at zero
+    MPJ_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    MPJ_TRY(copy_f64(Z, ldz, m, n, Q, ldq, s));
+    MPJ_TRY(mgs_inplace(Q, m, n, ldq, scratch, flag, s));
+    int fl = 0;
+    MPJ_CUDA_TRY(cudaMemcpyAsync(&fl, flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+    return fl ? MPJ_RANK_DEFICIENT : MPJ_SUCCESS;
+}
+
