@@ -69,7 +69,7 @@ struct HostScratch {
 enum ProfClass {
     PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
-    PC_APPLY1_F64, PC_AUX, kProfClasses
+    PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -128,6 +128,7 @@ int copy_pad_f64(const double* A, int lda, int rows, int cols, double* T, int ld
                  int Cpad, bool identity_pad, cudaStream_t s);
 int copy_pad_f32(const double* A, int lda, int rows, int cols, float* T, int ldt, int Rpad,
                  int Cpad, bool identity_pad, cudaStream_t s);
+int scale_pow2_f64(double* A, int ld, int rows, int cols, int e, cudaStream_t s);
 int set_identity_f64(double* V, int ld, int rows, int cols, cudaStream_t s);
 int set_identity_f32(float* V, int ld, int rows, int cols, cudaStream_t s);
 int copy_f64(const double* src, int lds, int rows, int cols, double* dst, int ldd, cudaStream_t s);

@@ -15,7 +15,8 @@
 
 namespace mpj {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;       // tile kernels: a 16 x 16 thread grid
+constexpr int kSolveThreads = 512;  // block-pair solves: more threads per inner round
 
 // Player at position `pos` (0 <= pos < P, P even) in round r of the circle method:
 // position 0 holds player 0, the others rotate through players 1..P-1.
@@ -57,7 +58,7 @@ struct InnerLayout {
 // (Remark 3.7) or |s_pq| <= tau (entries that cannot matter for the stopping
 // test).  Stops after an inner sweep with no rotation or after max_inner
 // sweeps.  Returns the number of rotations applied (all threads).
-// Must be called by all kThreads threads of the block.
+// Must be called by all threads of the block (any multiple of 32, at least 256).
 template <class Real, int M>
 __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real tau, int max_inner) {
     constexpr int LD = M + 1;
@@ -95,7 +96,7 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
             }
             __syncthreads();
             // two-sided update of the 2x2 blocks (a, b), a <= b, mirrored below the diagonal
-            for (int t = tid; t < P * P; t += kThreads) {
+            for (int t = tid; t < P * P; t += blockDim.x) {
                 int a = t / P, b = t % P;
                 if (a > b) continue;
                 int pa = ip[a], qa = iq[a];
@@ -129,7 +130,7 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
                 }
             }
             // F <- F J + (J - I): columns p, q of every rotation
-            for (int t = tid; t < M * P; t += kThreads) {
+            for (int t = tid; t < M * P; t += blockDim.x) {
                 int row = t % M, a = t / M;
                 if (sk[a]) continue;
                 int pa = ip[a], qa = iq[a];
@@ -162,74 +163,94 @@ template <class Real, int M>
 __device__ void reorthogonalise(Real* F, Real* G) {
     constexpr int LD = M + 1;
     constexpr int RM = M / 16;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const bool active = threadIdx.x < 256;             // a 16 x 16 grid of RM x RM patches
+    const int tx = threadIdx.x & 15, ty = (threadIdx.x >> 4) & 15;
     Real acc[RM][RM];
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) acc[i][j] = Real(0);
-    for (int k = 0; k < M; ++k) {
-        Real a[RM], b[RM];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = F[(ty * RM + i) * LD + k];   // F[k][R]
-#pragma unroll
-        for (int j = 0; j < RM; ++j) b[j] = F[(tx * RM + j) * LD + k];   // F[k][C]
+    if (active) {
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
+            for (int j = 0; j < RM; ++j) acc[i][j] = Real(0);
+        for (int k = 0; k < M; ++k) {
+            Real a[RM], b[RM];
 #pragma unroll
-    for (int i = 0; i < RM; ++i)
+            for (int i = 0; i < RM; ++i) a[i] = F[(ty * RM + i) * LD + k];   // F[k][R]
 #pragma unroll
-        for (int j = 0; j < RM; ++j) {
-            int R = ty * RM + i, C = tx * RM + j;
-            G[C * LD + R] = (F[C * LD + R] + F[R * LD + C]) + acc[i][j];
+            for (int j = 0; j < RM; ++j) b[j] = F[(tx * RM + j) * LD + k];   // F[k][C]
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RM; ++j) {
+                int R = ty * RM + i, C = tx * RM + j;
+                G[C * LD + R] = (F[C * LD + R] + F[R * LD + C]) + acc[i][j];
+            }
+    }
     __syncthreads();
     // acc = (F G)[R][C]
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) acc[i][j] = Real(0);
-    for (int k = 0; k < M; ++k) {
-        Real a[RM], b[RM];
-#pragma unroll
-        for (int i = 0; i < RM; ++i) a[i] = F[k * LD + ty * RM + i];     // F[R][k]
-#pragma unroll
-        for (int j = 0; j < RM; ++j) b[j] = G[(tx * RM + j) * LD + k];   // G[k][C]
+    if (active) {
 #pragma unroll
         for (int i = 0; i < RM; ++i)
 #pragma unroll
-            for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+            for (int j = 0; j < RM; ++j) acc[i][j] = Real(0);
+        for (int k = 0; k < M; ++k) {
+            Real a[RM], b[RM];
+#pragma unroll
+            for (int i = 0; i < RM; ++i) a[i] = F[k * LD + ty * RM + i];     // F[R][k]
+#pragma unroll
+            for (int j = 0; j < RM; ++j) b[j] = G[(tx * RM + j) * LD + k];   // G[k][C]
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < RM; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
     }
     __syncthreads();
+    if (active) {
 #pragma unroll
-    for (int i = 0; i < RM; ++i)
+        for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < RM; ++j) {
-            int R = ty * RM + i, C = tx * RM + j;
-            F[C * LD + R] = F[C * LD + R] - Real(0.5) * (G[C * LD + R] + acc[i][j]);
-        }
+            for (int j = 0; j < RM; ++j) {
+                int R = ty * RM + i, C = tx * RM + j;
+                F[C * LD + R] = F[C * LD + R] - Real(0.5) * (G[C * LD + R] + acc[i][j]);
+            }
+    }
     __syncthreads();
 }
 
 // Block solve epilogue shared by the two engines: optionally re-orthogonalise
-// W = I + F (when max |F| >= gate), then store F row-major to Fout.
+// W = I + F (when max |F| >= gate), then store F row-major to Fout and, when
+// fmax_out is given, max |F| (as a float) to *fmax_out -- the apply kernels use
+// it to pick the arithmetic of the tile products.
 template <class Real, int M>
-__device__ void finish_block(Real* F, Real* G, Real* Fout, Real gate, int* flag) {
+__device__ void finish_block(Real* F, Real* G, Real* Fout, Real gate, int* flag, float* fmax_out) {
     constexpr int LD = M + 1;
-    if (threadIdx.x == 0) flag[0] = 0;
+    if (threadIdx.x == 0) { flag[0] = 0; flag[1] = 0; }
     __syncthreads();
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
         int r = t % M, c = t / M;
         if (rabs(F[c * LD + r]) >= gate) flag[0] = 1;
     }
     __syncthreads();
     if (flag[0]) reorthogonalise<Real, M>(F, G);
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+    float mx = 0.f;
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
         int k = t / M, c = t % M;
-        Fout[t] = F[c * LD + k];                 // row-major: Fout[k*M + c] = F[k][c]
+        Real v = F[c * LD + k];
+        Fout[t] = v;                             // row-major: Fout[k*M + c] = F[k][c]
+        float a = (float)rabs(v);
+        mx = a > mx ? a : mx;
+    }
+    if (fmax_out) {
+        // non-negative floats order like their bit patterns
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<unsigned int*>(flag + 1), __float_as_uint(mx));
+        __syncthreads();
+        if (threadIdx.x == 0) *fmax_out = __uint_as_float(reinterpret_cast<unsigned int*>(flag)[1]);
     }
 }
 

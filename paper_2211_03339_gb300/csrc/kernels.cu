@@ -97,6 +97,22 @@ int copy_pad_f32(const double* A, int lda, int rows, int cols, float* T, int ldt
     return MPJ_SUCCESS;
 }
 
+__global__ void k_scale_pow2(double* A, int ld, int rows, int cols, int e) {
+    size_t total = (size_t)rows * cols;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < total;
+         t += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(t % rows), c = (int)(t / rows);
+        double* p = A + (size_t)r + (size_t)c * ld;
+        *p = scalbn(*p, e);
+    }
+}
+int scale_pow2_f64(double* A, int ld, int rows, int cols, int e, cudaStream_t s) {
+    MPJ_PROF(PC_AUX, s);
+    k_scale_pow2<<<grid_for((size_t)rows * cols), kThreads, 0, s>>>(A, ld, rows, cols, e);
+    MPJ_LAUNCH_CHECK("k_scale_pow2");
+    return MPJ_SUCCESS;
+}
+
 template <class Out>
 __global__ void k_identity(Out* V, int ld, int rows, int cols) {
     size_t total = (size_t)rows * cols;

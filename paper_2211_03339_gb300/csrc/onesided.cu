@@ -24,15 +24,24 @@ namespace mpj {
 // compensated inner products of Ogita, Rump and Oishi (Dot2, SIAM J. Sci.
 // Comput. 2005): the result is as accurate as if computed in twice the working
 // precision and then rounded.
+// Rounded arithmetic that nvcc may not contract into FMAs (the error-free
+// transforms below depend on every product and sum being rounded separately).
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rsub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rsub(float a, float b) { return __fsub_rn(a, b); }
+
 template <class Real>
 __device__ __forceinline__ void dot2_step(Real a, Real b, Real& s, Real& c) {
-    Real p = a * b;
+    Real p = rmul(a, b);
     Real pe = fma(a, b, -p);
-    Real t = s + p;
-    Real z = t - s;
-    Real e = (s - (t - z)) + (p - z);
+    Real t = radd(s, p);
+    Real z = rsub(t, s);
+    Real e = radd(rsub(s, rsub(t, z)), rsub(p, z));
     s = t;
-    c += pe + e;
+    c = radd(c, radd(pe, e));
 }
 
 // Partial Gram of pair `blockIdx.x` over rows [split*rows_per, ...) of C.  With
@@ -102,14 +111,14 @@ k_gram1(const Real* __restrict__ C, size_t ldc, int m, int N, int round, int row
 #pragma unroll
         for (int j = 0; j < RM; ++j) {
             size_t idx = base + (size_t)(tx * RM + j) * M + ty * RM + i;
-            Real h = acc[i][j] + cmp[i][j];
+            Real h = radd(acc[i][j], cmp[i][j]);
             Ghi[idx] = h;
-            Glo[idx] = cmp[i][j] - (h - acc[i][j]);
+            Glo[idx] = rsub(cmp[i][j], rsub(h, acc[i][j]));
         }
 }
 
 template <class Real, int B>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kSolveThreads)
 k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
          Real* __restrict__ Fbuf, Real tol_rot,
          Real gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
@@ -123,15 +132,15 @@ k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
     int* ip = reinterpret_cast<int*>(cs + 4 * (M / 2));
     int* flag = ip + 3 * (M / 2) + 2;
     const size_t off = (size_t)blockIdx.x * nsplit * M * M;
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
         int r = t % M, c = t / M;
         // compensated sum of the split partials (hi + lo pairs)
         Real sacc = Real(0), cacc = Real(0);
         for (int sp = 0; sp < nsplit; ++sp) {
             size_t idx = off + (size_t)sp * M * M + (size_t)c * M + r;
             Real p = Ghi[idx];
-            Real tt = sacc + p, z = tt - sacc;
-            cacc += (sacc - (tt - z)) + (p - z) + Glo[idx];
+            Real tt = radd(sacc, p), z = rsub(tt, sacc);
+            cacc = radd(cacc, radd(radd(rsub(sacc, rsub(tt, z)), rsub(p, z)), Glo[idx]));
             sacc = tt;
         }
         S[c * LD + r] = sacc + cacc;
@@ -139,7 +148,7 @@ k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
     }
     __syncthreads();
     int applied = inner_jacobi<Real, M>(S, F, cs, ip, tol_rot, Real(0), max_inner);
-    finish_block<Real, M>(F, G2, Fbuf + (size_t)blockIdx.x * M * M, gate, flag);
+    finish_block<Real, M>(F, G2, Fbuf + (size_t)blockIdx.x * M * M, gate, flag, nullptr);
     if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
 }
 
@@ -214,7 +223,7 @@ static int launch_round1(Real* C, int ldc, Real* V, int m, int N, Real* Wbuf, Re
     k_gram1<Real, B><<<g, kThreads, 0, s>>>(C, (size_t)ldc, m, N, r, rows_per, Ghi, Glo, nsplit, comp); }
     MPJ_LAUNCH_CHECK("k_gram1");
     { MPJ_PROF(sizeof(Real) == 8 ? PC_SOLVE1_F64 : PC_SOLVE1_F32, s);
-    k_solve1<Real, B><<<K, kThreads, InnerLayout<Real, M>::bytes, s>>>(Ghi, Glo, nsplit, Wbuf, tol_rot,
+    k_solve1<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(Ghi, Glo, nsplit, Wbuf, tol_rot,
                                                                       gate, max_inner, rot); }
     MPJ_LAUNCH_CHECK("k_solve1");
     int n_ctiles = ((m + M - 1) / M) * K;

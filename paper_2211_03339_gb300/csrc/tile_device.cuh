@@ -4,6 +4,8 @@
 // patch of the M x M result (RM = M/16).
 #pragma once
 
+#include <type_traits>
+
 #include "jacobi_device.cuh"
 
 namespace mpj {
@@ -104,4 +106,138 @@ __device__ void right_multiply_rows(Real* X, size_t ldx, int nrows, int row0, in
     }
 }
 
+// ---------------------------------------------------------------- double-float products
+// When the block rotations of a round are small (|F| <= 2^-8, the preconditioned
+// sweeps), the FP64 tile products X F are formed on the FP32 pipe (about 70 times
+// the FP64 rate on GB300) in double-float arithmetic: X and F are split into
+// float pairs (hi + lo, 48 significant bits), every product hi*hi is made exact
+// with an FMA (TwoProd), the cross terms hi*lo + lo*hi are added to the error
+// term, and the sum is accumulated with Knuth's TwoSum into a float pair.  The
+// relative error of X F is then ~2^-45, i.e. an absolute error below 2^-53 |X|
+// when |F| <= 2^-8, at the level of the FP64 rounding of the final sum X + X F.
+// The _rn intrinsics keep nvcc from contracting the transforms into FMAs.
+
+__device__ __forceinline__ void split_df(double v, float& h, float& l) {
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - (double)h);
+}
+
+// ah/al[i][j] = double-float sum_k A[k][ty*RM+i] * B[k][tx*RM+j] with the float
+// planes (Ah, Al), (Bh, Bl) laid out like tile_mm's operands (ld LDSF).
+template <int M, int LDSF>
+__device__ __forceinline__ void tile_mm_df(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                           const float* __restrict__ Bh, const float* __restrict__ Bl,
+                                           float (&ah)[M / 16][M / 16], float (&al)[M / 16][M / 16]) {
+    constexpr int RM = M / 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) { ah[i][j] = 0.f; al[i][j] = 0.f; }
+#pragma unroll 2
+    for (int k = 0; k < M; ++k) {
+        float a0[RM], a1[RM], b0[RM], b1[RM];
+#pragma unroll
+        for (int i = 0; i < RM; ++i) { a0[i] = Ah[k * LDSF + ty * RM + i]; a1[i] = Al[k * LDSF + ty * RM + i]; }
+#pragma unroll
+        for (int j = 0; j < RM; ++j) { b0[j] = Bh[k * LDSF + tx * RM + j]; b1[j] = Bl[k * LDSF + tx * RM + j]; }
+#pragma unroll
+        for (int i = 0; i < RM; ++i)
+#pragma unroll
+            for (int j = 0; j < RM; ++j) {
+                float p = __fmul_rn(a0[i], b0[j]);
+                float e = __fmaf_rn(a0[i], b0[j], -p);          // TwoProd: a0 b0 = p + e exactly
+                e = __fmaf_rn(a0[i], b1[j], e);
+                e = __fmaf_rn(a1[i], b0[j], e);
+                float sh = __fadd_rn(ah[i][j], p);              // TwoSum(ah, p)
+                float bb = __fsub_rn(sh, ah[i][j]);
+                float er = __fadd_rn(__fsub_rn(ah[i][j], __fsub_rn(sh, bb)), __fsub_rn(p, bb));
+                ah[i][j] = sh;
+                al[i][j] = __fadd_rn(al[i][j], __fadd_rn(er, e));
+            }
+    }
+}
+
+// Split the FP64 matrix D (ld LDSD, D[k*LDSD + c]) into float planes H, L (ld LDSF).
+template <int M, int LDSD, int LDSF>
+__device__ __forceinline__ void split_tile(const double* D, float* H, float* L) {
+    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+        int k = t / M, c = t % M;
+        float h, l;
+        split_df(D[k * LDSD + c], h, l);
+        H[k * LDSF + c] = h;
+        L[k * LDSF + c] = l;
+    }
+}
+
+// Rows [row0, row0+M) of X restricted to the columns of pair (Ib, Jb) times
+// W_b = I + F_b in delta form, with the product X F_b in double-float
+// arithmetic (see tile_mm_df).  The FP64 sum X + X F_b is formed with the exact
+// X, which each thread reads into registers.  smem: 4 float planes of M*LDSF.
+template <int B>
+__device__ void right_multiply_rows_df(double* X, size_t ldx, int nrows, int row0, int Ib, int Jb,
+                                       const double* __restrict__ Fsrc, float* smf) {
+    constexpr int M = 2 * B;
+    constexpr int LDSF = M + 4;
+    constexpr int LDS = M + SmemPad<double>::value;
+    constexpr int RM = M / 16;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float* Xh = smf;
+    float* Xl = Xh + M * LDSF;
+    float* Fh = Xl + M * LDSF;
+    float* Fl = Fh + M * LDSF;
+    double xr[RM][RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) {
+            int gr = row0 + ty * RM + i;
+            xr[i][j] = gr < nrows ? X[(size_t)gr + (size_t)pair_global(tx * RM + j, Ib, Jb, B) * ldx] : 0.0;
+        }
+    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+        int r = t % M, kc = t / M;
+        int gr = row0 + r;
+        double v = gr < nrows ? X[(size_t)gr + (size_t)pair_global(kc, Ib, Jb, B) * ldx] : 0.0;
+        split_df(v, Xh[kc * LDSF + r], Xl[kc * LDSF + r]);
+        int k = t / M, c = t % M;
+        split_df(Fsrc[t], Fh[k * LDSF + c], Fl[k * LDSF + c]);     // Fsrc row-major
+    }
+    __syncthreads();
+    float ah[RM][RM], al[RM][RM];
+    tile_mm_df<M, LDSF>(Xh, Xl, Fh, Fl, ah, al);
+    double y[RM][RM];
+#pragma unroll
+    for (int i = 0; i < RM; ++i)
+#pragma unroll
+        for (int j = 0; j < RM; ++j) y[i][j] = xr[i][j] + ((double)ah[i][j] + (double)al[i][j]);
+    __syncthreads();
+    double* Ys = reinterpret_cast<double*>(smf);
+    tile_store_colmajor<double, M, LDS>(Ys, y);
+    __syncthreads();
+    for (int t = threadIdx.x; t < M * M; t += kThreads) {
+        int r = t % M, c = t / M;
+        int gr = row0 + r;
+        if (gr < nrows) X[(size_t)gr + (size_t)pair_global(c, Ib, Jb, B) * ldx] = Ys[c * LDS + r];
+    }
+}
+
+// Gather the tile T[IJ_a, IJ_b] (rows from pair a, columns from pair b) into
+// Xs[k*LDS + r] with 16-byte loads: each half column is b contiguous entries.
+template <class Real, int B>
+__device__ __forceinline__ void gather_tile(Real* Xs, const Real* __restrict__ T, int N, int Ia, int Ja,
+                                            int Ib, int Jb) {
+    constexpr int M = 2 * B;
+    constexpr int LDS = M + SmemPad<Real>::value;
+    constexpr int VEC = 16 / sizeof(Real);
+    using V4 = typename std::conditional<sizeof(Real) == 8, double2, float4>::type;
+    for (int t = threadIdx.x; t < M * M / VEC; t += kThreads) {
+        int rv = t % (M / VEC), kc = t / (M / VEC);
+        int r = rv * VEC;
+        V4 v = *reinterpret_cast<const V4*>(
+            T + (size_t)pair_global(r, Ia, Ja, B) + (size_t)pair_global(kc, Ib, Jb, B) * N);
+        *reinterpret_cast<V4*>(Xs + kc * LDS + r) = v;
+    }
+}
+
 }  // namespace mpj
+
