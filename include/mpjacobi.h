@@ -130,6 +130,41 @@ int mpj_gesvj_plain(const double* A, int m, int n, int lda, double* Sigma, doubl
 size_t mpj_gesvj_workspace_bytes(int m, int n);
 
 /* ------------------------------------------------------------------------
+ * Batched eigendecompositions: many independent symmetric matrices, each
+ * solved by Algorithm 4.1 (method 1) or Algorithm 3.2 (method 0), in one
+ * persistent kernel launch (one CTA per matrix at a time, atomic work queue,
+ * largest matrices first).  Sizes 1 <= n_i <= 256.
+ *
+ * Packed layouts (device, column-major, ld n_i): A_i and V_i start at offset
+ * sum_{j<i} n_j^2, Lambda_i (ascending) at sum_{j<i} n_j.
+ *
+ * mpj_batch_plan_create: ns is a HOST array of the count sizes.  Allocates the
+ *   job list and one scratch slot per resident CTA (about 2.7 MB each; see
+ *   mpj_batch_plan_info) on the current device; synchronous.
+ * mpj_syevj_batched: enqueues one memset and one kernel on `stream`, performs
+ *   no host synchronisation and no allocation (it may be captured in a CUDA
+ *   graph).  tol: relative tolerance of every matrix (<= 0: n_i * 2^-53).
+ *   status (optional, device, count ints): per-matrix MPJ_* code.
+ *   sweeps (optional, device, count ints): FP64 sweeps + 1000 * FP32 sweeps.
+ *   Runs of one plan must not overlap (they share the scratch and counter).
+ * ------------------------------------------------------------------------ */
+typedef struct mpj_batch_plan_s mpj_batch_plan;
+typedef struct mpj_batch_tuning {
+    int ctas_per_sm;        /* 1 or 2 (default 2)                               */
+    int max_inner;          /* inner sweeps per block solve for n > 2b (def. 1)  */
+    int block_large;        /* block size b for n > 64: 16 or 32 (default 32)    */
+    int max_sweeps;         /* FP64 sweeps cap (default 40)                      */
+    int max_sweeps_stage1;  /* FP32 sweeps cap (default 40)                      */
+} mpj_batch_tuning;
+int mpj_batch_plan_create(const int* ns, int count, int method, const mpj_batch_tuning* tuning,
+                          mpj_batch_plan** plan);
+int mpj_batch_plan_info(const mpj_batch_plan* plan, long long* a_elems, long long* lambda_elems,
+                        int* ctas, size_t* scratch_bytes);
+int mpj_syevj_batched(mpj_batch_plan* plan, const double* A, double* Lambda, double* V, double tol,
+                      int* status, int* sweeps, void* stream);
+void mpj_batch_plan_destroy(mpj_batch_plan* plan);
+
+/* ------------------------------------------------------------------------
  * Single steps of the pipeline, exposed for stage-wise checks.
  * ------------------------------------------------------------------------ */
 

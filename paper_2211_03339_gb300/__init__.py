@@ -40,6 +40,8 @@ EXPORTS = ["mpj_syevj_mp", "mpj_syevj_plain", "mpj_syevj_workspace_bytes",
            "mpj_sweeps", "mpj_sweeps_workspace_bytes",
            "mpj_profile_enable", "mpj_profile_reset", "mpj_profile_read", "mpj_profile_name",
            "mpj_profile_classes", "mpj_kernel_launches",
+           "mpj_batch_plan_create", "mpj_batch_plan_info", "mpj_syevj_batched",
+           "mpj_batch_plan_destroy",
            "mpj_status_string", "mpj_last_error", "mpj_version"]
 
 
@@ -62,6 +64,13 @@ class Options(ctypes.Structure):
     _fields_ = [("max_sweeps", ctypes.c_int), ("max_sweeps_stage1", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("tol_stage1", ctypes.c_double),
                 ("ju_ratio", ctypes.c_double), ("block", ctypes.c_int)]
+
+
+class BatchTuning(ctypes.Structure):
+    """Mirror of ``mpj_batch_tuning`` (zero fields mean 'default')."""
+    _fields_ = [("ctas_per_sm", ctypes.c_int), ("max_inner", ctypes.c_int),
+                ("block_large", ctypes.c_int), ("max_sweeps", ctypes.c_int),
+                ("max_sweeps_stage1", ctypes.c_int)]
 
 
 class MPJError(RuntimeError):
@@ -116,6 +125,14 @@ def lib():
         L.mpj_profile_name.argtypes = [i]; L.mpj_profile_name.restype = ctypes.c_char_p
         L.mpj_profile_classes.argtypes = []; L.mpj_profile_classes.restype = i
         L.mpj_kernel_launches.argtypes = []; L.mpj_kernel_launches.restype = ctypes.c_ulonglong
+        L.mpj_batch_plan_create.argtypes = [p, i, i, ctypes.POINTER(BatchTuning), ctypes.POINTER(p)]
+        L.mpj_batch_plan_create.restype = i
+        L.mpj_batch_plan_info.argtypes = [p, ctypes.POINTER(ctypes.c_longlong),
+                                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(i),
+                                          ctypes.POINTER(sz)]
+        L.mpj_batch_plan_info.restype = i
+        L.mpj_syevj_batched.argtypes = [p, p, p, p, d, p, p, p]; L.mpj_syevj_batched.restype = i
+        L.mpj_batch_plan_destroy.argtypes = [p]; L.mpj_batch_plan_destroy.restype = None
         _lib = L
         return L
 
@@ -313,3 +330,61 @@ def profile_read():
 
 def kernel_launches():
     return int(lib().mpj_kernel_launches())
+
+
+# ---------------------------------------------------------------- batched solver
+class BatchPlan:
+    """Plan for many independent eigendecompositions (n_i <= 256) in one launch.
+
+    ``ns``: the sizes; ``method``: "mp" (Alg. 4.1) or "plain" (Alg. 3.2).  The
+    packed layouts (column-major, ld n_i) are: A_i and V_i at offset
+    sum_{j<i} n_j^2, Lambda_i at sum_{j<i} n_j.  ``run`` enqueues one memset and
+    one kernel on the current stream (no host synchronisation, capturable).
+    """
+
+    def __init__(self, ns, method="mp", tuning=None):
+        import numpy as np
+        self.ns = np.asarray(ns, dtype=np.int32)
+        self.method = 1 if method == "mp" else 0
+        arr = (ctypes.c_int * len(self.ns))(*[int(x) for x in self.ns])
+        handle = ctypes.c_void_p()
+        tun = None
+        if tuning is not None:
+            tun = tuning if isinstance(tuning, BatchTuning) else BatchTuning(**tuning)
+        rc = lib().mpj_batch_plan_create(ctypes.cast(arr, ctypes.c_void_p), len(self.ns), self.method,
+                                         ctypes.byref(tun) if tun is not None else None,
+                                         ctypes.byref(handle))
+        _check(rc, "mpj_batch_plan_create")
+        self.handle = handle
+        a, l, c, b = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_int(), ctypes.c_size_t()
+        lib().mpj_batch_plan_info(handle, ctypes.byref(a), ctypes.byref(l), ctypes.byref(c), ctypes.byref(b))
+        self.a_elems, self.lambda_elems, self.ctas, self.scratch_bytes = a.value, l.value, c.value, b.value
+        self.a_offsets = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64) ** 2)])[:-1]
+        self.l_offsets = np.concatenate([[0], np.cumsum(self.ns.astype(np.int64))])[:-1]
+
+    def outputs(self, device="cuda"):
+        torch = _torch()
+        return (torch.empty(self.lambda_elems, dtype=torch.float64, device=device),
+                torch.empty(self.a_elems, dtype=torch.float64, device=device),
+                torch.empty(len(self.ns), dtype=torch.int32, device=device),
+                torch.empty(len(self.ns), dtype=torch.int32, device=device))
+
+    def run(self, A_packed, Lam, V, status=None, sweeps=None, tol=0.0):
+        """Enqueue the batched solve of the packed A on the current stream."""
+        rc = lib().mpj_syevj_batched(self.handle, _ptr(A_packed), _ptr(Lam), _ptr(V), float(tol),
+                                     _ptr(status) if status is not None else None,
+                                     _ptr(sweeps) if sweeps is not None else None,
+                                     _stream_ptr(A_packed.device))
+        _check(rc, "mpj_syevj_batched")
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.mpj_batch_plan_destroy(h)
+            self.handle = None
+
+
+def pack_symmetric(mats):
+    """Concatenate column-major copies of square float64 numpy matrices."""
+    import numpy as np
+    return np.concatenate([np.asarray(M, dtype=np.float64).ravel(order="F") for M in mats])

@@ -19,8 +19,7 @@
 
 #include "internal.h"
 #include <cstdlib>
-#include "jacobi_device.cuh"
-#include "tile_device.cuh"
+#include "engine_device.cuh"
 
 namespace mpj {
 
@@ -29,209 +28,29 @@ __global__ void __launch_bounds__(kSolveThreads)
 k_solve2(Real* __restrict__ T, int N, Real* __restrict__ Fbuf, float* __restrict__ fmax, int round,
          Real eps, Real tau, Real gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
     constexpr int M = 2 * B;
-    constexpr int LD = M + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
-    Real* S = reinterpret_cast<Real*>(smraw);
-    Real* F = S + M * LD;
-    Real* G = F + M * LD;
-    Real* cs = G + M * LD;
-    int* ip = reinterpret_cast<int*>(cs + 4 * (M / 2));
-    int* flag = ip + 3 * (M / 2) + 2;
-    const int nblocks = N / B;
-    int I, J;
-    round_pair(round, blockIdx.x, nblocks, I, J);
-    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
-        int r = t % M, c = t / M;
-        S[c * LD + r] = T[(size_t)pair_global(r, I, J, B) + (size_t)pair_global(c, I, J, B) * N];
-        F[c * LD + r] = Real(0);
-    }
-    __syncthreads();
-    int applied = inner_jacobi<Real, M>(S, F, cs, ip, eps, tau, max_inner);
-    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
-        int r = t % M, c = t / M;
-        T[(size_t)pair_global(r, I, J, B) + (size_t)pair_global(c, I, J, B) * N] = S[c * LD + r];
-    }
-    finish_block<Real, M>(F, G, Fbuf + (size_t)blockIdx.x * M * M, gate, flag, fmax + blockIdx.x);
+    int applied = pair_solve<Real, B>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
+                                      Fbuf + (size_t)blockIdx.x * M * M, fmax + blockIdx.x, smraw);
     if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
 }
 
-// Tile (a, b), a < b, of the current pairing: decode from the linear tile index.
-__device__ __forceinline__ void decode_tile(int tile, int K, int& a, int& b) {
-    a = 0;
-    int rem = tile;
-    while (rem >= K - 1 - a) { rem -= K - 1 - a; ++a; }
-    b = a + 1 + rem;
-}
-
-// Shared memory of the tile kernels: FP path 3 (T) or 2 (V) planes of M*LDS
-// Real; double-float path 6 (T) or 4 (V) float planes of M*(M+4).
-template <class Real, int B>
-struct ApplySmem {
-    static constexpr int M = 2 * B;
-    static constexpr size_t fp_t = sizeof(Real) * 3 * M * (M + SmemPad<Real>::value);
-    static constexpr size_t fp_v = sizeof(Real) * 2 * M * (M + SmemPad<Real>::value);
-    static constexpr size_t df_t = sizeof(Real) == 8 ? sizeof(float) * 6 * M * (M + 4) : 0;
-    static constexpr size_t df_v = sizeof(Real) == 8 ? sizeof(float) * 4 * M * (M + 4) : 0;
-    static constexpr size_t t = fp_t > df_t ? fp_t : df_t;
-    static constexpr size_t v = fp_v > df_v ? fp_v : df_v;
-};
-
-// Double-float version of the off-diagonal tile update (Real = double only).
-template <int B>
-__device__ void apply_tile_df(double* T, int N, const double* __restrict__ Fbuf, int a, int b,
-                              int Ia, int Ja, int Ib, int Jb, float* smf) {
-    constexpr int M = 2 * B;
-    constexpr int LDSF = M + 4;
-    constexpr int LDS = M + SmemPad<double>::value;
-    constexpr int RM = M / 16;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    float* Xh = smf;
-    float* Xl = Xh + M * LDSF;
-    float* Bh = Xl + M * LDSF;     // F_b, then Z
-    float* Bl = Bh + M * LDSF;
-    float* Ah = Bl + M * LDSF;     // F_a
-    float* Al = Ah + M * LDSF;
-    const double* Fb = Fbuf + (size_t)b * M * M;
-    const double* Fa = Fbuf + (size_t)a * M * M;
-    double z[RM][RM];
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j)
-            z[i][j] = T[(size_t)pair_global(ty * RM + i, Ia, Ja, B) +
-                        (size_t)pair_global(tx * RM + j, Ib, Jb, B) * N];
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
-        int r = t % M, kc = t / M;
-        double v = T[(size_t)pair_global(r, Ia, Ja, B) + (size_t)pair_global(kc, Ib, Jb, B) * N];
-        split_df(v, Xh[kc * LDSF + r], Xl[kc * LDSF + r]);
-        int k = t / M, c = t % M;
-        split_df(Fb[t], Bh[k * LDSF + c], Bl[k * LDSF + c]);
-        split_df(Fa[t], Ah[k * LDSF + c], Al[k * LDSF + c]);
-    }
-    __syncthreads();
-    float ah[RM][RM], al[RM][RM];
-    tile_mm_df<M, LDSF>(Xh, Xl, Bh, Bl, ah, al);                  // X F_b
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) z[i][j] += (double)ah[i][j] + (double)al[i][j];
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) {
-            int R = ty * RM + i, C = tx * RM + j;
-            split_df(z[i][j], Bh[R * LDSF + C], Bl[R * LDSF + C]);  // Z row-major
-        }
-    __syncthreads();
-    tile_mm_df<M, LDSF>(Ah, Al, Bh, Bl, ah, al);                  // F_a^T Z
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) z[i][j] += (double)ah[i][j] + (double)al[i][j];
-    __syncthreads();
-    double* Ys = reinterpret_cast<double*>(smf);                  // col-major
-    double* Yr = Ys + M * LDS;                                    // row-major
-    tile_store_colmajor<double, M, LDS>(Ys, z);
-    tile_store_rowmajor<double, M, LDS>(Yr, z);
-    __syncthreads();
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
-        int r = t % M, c = t / M;
-        T[(size_t)pair_global(r, Ia, Ja, B) + (size_t)pair_global(c, Ib, Jb, B) * N] = Ys[c * LDS + r];
-        int c2 = t % M, r2 = t / M;
-        T[(size_t)pair_global(c2, Ib, Jb, B) + (size_t)pair_global(r2, Ia, Ja, B) * N] = Yr[r2 * LDS + c2];
-    }
-}
-
-// Off-diagonal tiles in delta form: Z = X + X F_b, Y = Z + F_a^T Z = W_a^T X W_b.
-// A tile whose two block rotations have max |F| <= df_gate is computed in
-// double-float arithmetic (Real = double), the others in Real.
 template <class Real, int B>
 __global__ void __launch_bounds__(kThreads)
 k_apply2T(Real* __restrict__ T, int N, const Real* __restrict__ Fbuf, const float* __restrict__ fmax,
           int round, float df_gate) {
-    constexpr int M = 2 * B;
-    constexpr int LDS = M + SmemPad<Real>::value;
-    constexpr int RM = M / 16;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int nblocks = N / B;
-    const int K = nblocks / 2;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     int a, b;
-    decode_tile(blockIdx.x, K, a, b);
-    int Ia, Ja, Ib, Jb;
-    round_pair(round, a, nblocks, Ia, Ja);
-    round_pair(round, b, nblocks, Ib, Jb);
-    const float fa = fmax[a], fb = fmax[b];
-    if (fa == 0.f && fb == 0.f) return;              // W_a = W_b = I: the tile is unchanged
-    if constexpr (sizeof(Real) == 8) {
-        if (fa <= df_gate && fb <= df_gate) {
-            apply_tile_df<B>(reinterpret_cast<double*>(T), N, reinterpret_cast<const double*>(Fbuf),
-                             a, b, Ia, Ja, Ib, Jb, reinterpret_cast<float*>(smraw));
-            return;
-        }
-    }
-    Real* Xs = reinterpret_cast<Real*>(smraw);
-    Real* Fb = Xs + M * LDS;     // F_b, then Z
-    Real* Fa = Fb + M * LDS;
-    gather_tile<Real, B>(Xs, T, N, Ia, Ja, Ib, Jb);
-    load_w<Real, M, LDS>(Fb, Fbuf, b);
-    load_w<Real, M, LDS>(Fa, Fbuf, a);
-    __syncthreads();
-    Real acc[M / 16][M / 16];
-    tile_mm<Real, M, LDS>(Xs, Fb, acc);              // (X F_b)[r][c]
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) acc[i][j] += Xs[(tx * RM + j) * LDS + ty * RM + i];
-    __syncthreads();
-    tile_store_rowmajor<Real, M, LDS>(Fb, acc);      // Z row-major over F_b
-    __syncthreads();
-    tile_mm<Real, M, LDS>(Fa, Fb, acc);              // (F_a^T Z)[r][c]
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) acc[i][j] += Fb[(ty * RM + i) * LDS + tx * RM + j];
-    __syncthreads();
-    tile_store_colmajor<Real, M, LDS>(Xs, acc);      // Xs[c*LDS + r]
-    tile_store_rowmajor<Real, M, LDS>(Fb, acc);      // Fb[r*LDS + c]
-    __syncthreads();
-    for (int t = threadIdx.x; t < M * M; t += kThreads) {
-        int r = t % M, c = t / M;
-        T[(size_t)pair_global(r, Ia, Ja, B) + (size_t)pair_global(c, Ib, Jb, B) * N] = Xs[c * LDS + r];
-        int c2 = t % M, r2 = t / M;                  // mirrored tile, coalesced in c2
-        T[(size_t)pair_global(c2, Ib, Jb, B) + (size_t)pair_global(r2, Ia, Ja, B) * N] =
-            Fb[r2 * LDS + c2];
-    }
+    decode_tile(blockIdx.x, N / (2 * B), a, b);
+    apply_tile<Real, B>(T, N, Fbuf, fmax, round, a, b, df_gate, smraw);
 }
 
-// 2b-row slabs of V times the block rotation of their pair: V[:, IJ_b] (I + F_b).
 template <class Real, int B>
 __global__ void __launch_bounds__(kThreads)
 k_apply2V(Real* __restrict__ V, int N, const Real* __restrict__ Fbuf, const float* __restrict__ fmax,
           int round, float df_gate) {
-    constexpr int M = 2 * B;
-    constexpr int LDS = M + SmemPad<Real>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int nblocks = N / B;
-    const int K = nblocks / 2;
-    int rb = blockIdx.x / K, b = blockIdx.x % K;
-    int Ib, Jb;
-    round_pair(round, b, nblocks, Ib, Jb);
-    const float fb = fmax[b];
-    if (fb == 0.f) return;                           // W_b = I: the slab is unchanged
-    if constexpr (sizeof(Real) == 8) {
-        if (fb <= df_gate) {
-            right_multiply_rows_df<B>(reinterpret_cast<double*>(V), (size_t)N, N, rb * M, Ib, Jb,
-                                      reinterpret_cast<const double*>(Fbuf) + (size_t)b * M * M,
-                                      reinterpret_cast<float*>(smraw));
-            return;
-        }
-    }
-    Real* Xs = reinterpret_cast<Real*>(smraw);
-    Real* Fb = Xs + M * LDS;
-    load_w<Real, M, LDS>(Fb, Fbuf, b);
-    right_multiply_rows<Real, B>(V, (size_t)N, N, rb * M, Ib, Jb, Xs, Fb);
+    const int K = N / (2 * B);
+    apply_slab<Real, B>(V, N, Fbuf, fmax, round, blockIdx.x / K, blockIdx.x % K, df_gate, smraw);
 }
 
 // MPJ_DF_GATE overrides the double-float gate (a negative value disables the
