@@ -35,7 +35,7 @@ if ROOT not in sys.path:
 U = 2.0 ** -53
 METRIC = "n=4096 FP64-accurate eig time & batched solves/s: preconditioned vs plain Jacobi"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz
-PROFILE_FILE = os.path.join(ROOT, "profiles", "apply2_f64_n4096.md")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 
 
 def parse():
@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--spectrum", default="uniform")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch", type=int, default=10000, help="matrices in the batched workload")
     ap.add_argument("--once", action="store_true",
                     help="run one mpj_syevj_mp solve and exit (for profiler captures)")
     return ap.parse_args()
@@ -112,11 +114,12 @@ def source_sha():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(n):
-    """DRAM bytes per launch of apply2_f64 from the committed ncu summary, if it
-    was taken on the current kernel sources at this n (else None)."""
+def profiled_traffic(n, kclass):
+    """DRAM bytes per launch of a kernel class from its committed ncu summary
+    (profiles/<class>_n<n>.md), if it was taken on the current kernel sources
+    (else None)."""
     try:
-        txt = open(PROFILE_FILE).read()
+        txt = open(os.path.join(PROFILE_DIR, f"{kclass}_n{n}.md")).read()
     except OSError:
         return None
     m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
@@ -202,6 +205,57 @@ def accuracy(A, lam_true, L, V):
     err = float((L - lam_true).abs().max())
     return {"res_over_nu": res / (n * U), "orth_over_nu": orth / (n * U),
             "lamerr_over_nu_a2": err / (n * U * a2)}
+
+
+def run_batched(args, dev, world):
+    """Batched workload: args.batch matrices, n uniform in [8, 256], uniform spectra,
+    one persistent launch (schedule from the autotuner), mp and plain; beside it
+    the single-matrix path looped over a sample of 100 of the same matrices."""
+    import numpy as np
+    import torch
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import autotune, synth
+    sizes = synth.batch_sizes(args.batch, 8, 256, seed=synth.seed_for(3, 0))
+    mats = [synth.sym_matrix(int(n), "uniform", seed=synth.seed_for(3, 1000 + i))[0]
+            for i, n in enumerate(sizes)]
+    Ad = torch.from_numpy(mpj.pack_symmetric(mats)).to(dev)
+    out = {"workload": f"{args.batch} matrices, n uniform in [8,256], uniform spectrum, "
+                       "one persistent launch (CUDA graph)",
+           "mean_n": float(np.mean(sizes))}
+    for method in ("mp", "plain"):
+        tun, _ = autotune.tune(mats, method=method, sample=1000, use_cache=False)
+        plan = mpj.BatchPlan(sizes, method=method, tuning=tun)
+        Lam, V, st, sw = plan.outputs(dev)
+        stream = torch.cuda.Stream(dev)
+        with torch.cuda.stream(stream):
+            plan.run(Ad, Lam, V, st, sw)
+        torch.cuda.synchronize(dev)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            plan.run(Ad, Lam, V, st, sw)
+        g.replay(); torch.cuda.synchronize(dev)
+        times = []
+        for _ in range(2):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(); g.replay(); e1.record(); e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = min(times)
+        bad = int((st != 0).sum().item())
+        swh = sw.cpu().numpy()
+        out[method] = {"solves_per_s": world * args.batch / (ms / 1e3), "ms": ms, "tuning": tun,
+                       "nonzero_status": bad, "mean_fp64_sweeps": float(np.mean(swh % 1000)),
+                       "mean_fp32_sweeps": float(np.mean(swh // 1000))}
+        fn = mpj.syevj_mp if method == "mp" else mpj.syevj_plain
+        sample = [torch.from_numpy(mats[i]).to(dev) for i in range(100)]
+        fn(sample[0]); torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for a in sample:
+            fn(a)
+        e1.record(); e1.synchronize()
+        out[method]["loop_single_solves_per_s"] = 100 / (e0.elapsed_time(e1) / 1e3)
+        out[method]["speedup_vs_loop"] = out[method]["solves_per_s"] / out[method]["loop_single_solves_per_s"]
+    return out
 
 
 def run_ours(args):
@@ -315,34 +369,40 @@ def run_ours(args):
         plain = {"ms": pms, "sweeps": stp.sweeps, "speedup_mp_over_plain": pms / (total_ms / args.steps),
                  **accuracy(A, lam_true, L, Vc.t())}
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, dev, world)
+
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel (largest summed event time)
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    dname, (dlaunch, dms) = dom
-    B = stats["block"]
-    N = ((n + 2 * B - 1) // (2 * B)) * (2 * B)
-    K = N // (2 * B)
-    rounds = 2 * K - 1
-    roof = None
-    if dname == "apply2_f64" and dlaunch > 0:
-        avg_s = dms / dlaunch / 1e3
-        alg_flops = 6.0 * n ** 3 / rounds            # Alg. 3.2 sweep = 6 n^3 flops, one round per launch
-        M = 2 * B
-        realised = 2 * (2 * M ** 3) * (K * (K - 1) // 2) + 2 * M ** 3 * (N // M) * K
-        achieved = alg_flops / avg_s / 1e12
-        traffic = profiled_traffic(n)
-        roof = {"kernel": "k_apply2<double,%d>" % B, "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "launches": dlaunch, "avg_launch_ms": dms / dlaunch,
-                "alg_flops_per_launch": alg_flops, "realised_flops_per_launch": realised,
-                "realised_tflops": realised / avg_s / 1e12,
-                "peak_note": "FP64 SIMT: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal; "
-                             "probe measured 1.06 TFLOP/s at 1995 MHz)"}
-    else:
-        roof = {"kernel": dname, "bound": "alu", "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
+    # roofline of the dominant kernel class (largest summed event time among the
+    # classes with an algorithmic count; SURVEY-style per-solve counts:
+    # Alg. 3.2 sweep = 6 n^3 (3 n^3 for T, 3 n^3 for V), MGS 2 n^3 (projections n^3,
+    # trailing update n^3), congruence 3 n^3)
+    sw64, sw32 = stats["sweeps"], stats["sweeps_stage1"]
+    alg = {"dgemm_f64": 4.0 * n ** 3, "mgs_proj": 1.0 * n ** 3,
+           "apply2_f64": 3.0 * n ** 3 * sw64, "apply2v_f64": 3.0 * n ** 3 * sw64,
+           "apply2_f32": 3.0 * n ** 3 * sw32, "apply2v_f32": 3.0 * n ** 3 * sw32}
+    fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
+    df_peak = 152 * 128 / 11 * 2 * 2.070e9 / 1e12     # 11 FP32 instructions per double-float MAC
+    peaks = {"dgemm_f64": (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
+             "mgs_proj": (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
+             "apply2_f64": (df_peak, "double-float on FP32: 152 x 128 lanes / 11 instr per MAC x 2 x 2.07 GHz"),
+             "apply2v_f64": (df_peak, "double-float on FP32: 152 x 128 lanes / 11 instr per MAC x 2 x 2.07 GHz"),
+             "apply2_f32": (fp32_peak, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz"),
+             "apply2v_f32": (fp32_peak, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz")}
+    cands = {k: v for k, v in prof.items() if k in alg and v[0] > 0}
+    dname, (dlaunch, dms) = max(cands.items(), key=lambda kv: kv[1][1])
+    per_launch_alg = alg[dname] * args.steps / dlaunch
+    avg_s = dms / dlaunch / 1e3
+    achieved = per_launch_alg / avg_s / 1e12
+    pk, note = peaks[dname]
+    roof = {"kernel": dname, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "traffic": profiled_traffic(n, dname), "launches": dlaunch,
+            "avg_launch_ms": dms / dlaunch, "alg_flops_per_launch": per_launch_alg,
+            "peak_note": note + " (nominal; see DESIGN.md for the measured probe rates)",
+            "share_of_step": dms / total_ms}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -365,7 +425,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "stages_ms": stats["ms_stage"], "sweeps": stats["sweeps"],
         "sweeps_stage1": stats["sweeps_stage1"], "off_T0": stats["off_T0"],
-        "accuracy_mp": acc_mp, "plain": plain,
+        "accuracy_mp": acc_mp, "plain": plain, "batched": batched,
         "kernels_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
     }
     print(json.dumps(line), flush=True)
