@@ -129,6 +129,16 @@ def profiled_traffic(n, kclass):
     return float(m2.group(1))
 
 
+def max_over_ranks(value, pg, device="cpu"):
+    """Largest value over all ranks (the slowest rank's time); identity without a group."""
+    if pg is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -325,11 +335,7 @@ def run_ours(args):
     stats = st.as_dict()
     acc_mp = accuracy(A, lam_true, L, Vc.t())
     total_ms = sum(times)
-    t_max = total_ms
-    if pg is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(total_ms, pg, dev)
     value = world * args.steps / (t_max / 1e3)
 
     # end to end through the C ABI with host buffers: H2D of A, solve, D2H of Lambda and V
@@ -348,11 +354,7 @@ def run_ours(args):
         e1.synchronize()
         e2e_times.append(e0.elapsed_time(e1))
     e2e_ms = sum(e2e_times) / len(e2e_times)
-    e2e_max = e2e_ms
-    if pg is not None:
-        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_max = float(t.item())
+    e2e_max = max_over_ranks(e2e_ms, pg, dev)
 
     # plain Alg. 3.2 on the same matrix (the comparison the metric names)
     plain = None
