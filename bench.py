@@ -268,6 +268,44 @@ def run_batched(args, dev, world):
     return out
 
 
+def run_backward(args, dev):
+    """Differentiation workload: batch of 512 matrices, n in {64, 128}, gapped
+    uniform spectra; loss Sum w_i lambda_i + ||B V[:, :n/2]||_F^2; forward by the
+    batched solver (Alg. 4.1), backward by the hand-written kernel."""
+    import numpy as np
+    import torch
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import synth
+    out = {}
+    for n in (64, 128):
+        b = 512
+        A = torch.from_numpy(np.stack([synth.sym_matrix(n, "gapped", seed=synth.seed_for(5, i))[0]
+                                       for i in range(b)])).to(dev)
+        rng = synth.rng_for(synth.seed_for(5, 9999))
+        w = torch.from_numpy(rng.standard_normal((b, n))).to(dev)
+        Bm = torch.from_numpy(rng.standard_normal((b, 3, n))).to(dev)
+
+        def step():
+            Ag = A.clone().requires_grad_(True)
+            lam, V = mpj.eigh(Ag)
+            L = (w * lam).sum() + (torch.matmul(Bm, V[..., :, : n // 2]) ** 2).sum()
+            (g,) = torch.autograd.grad(L, Ag)
+            return g
+        step(); torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(); step(); e1.record(); e1.synchronize()
+        ms_fb = e0.elapsed_time(e1)
+        lam, V = mpj.eigh(A)
+        gl = torch.ones_like(lam); gV = torch.ones_like(V)
+        mpj.syev_backward(lam, V, gl, gV); torch.cuda.synchronize(dev)
+        e0.record(); mpj.syev_backward(lam, V, gl, gV); e1.record(); e1.synchronize()
+        ms_b = e0.elapsed_time(e1)
+        out[f"n{n}"] = {"batch": b, "fwd_bwd_ms": ms_fb, "bwd_kernel_ms": ms_b,
+                        "matrices_per_s_fwd_bwd": b / (ms_fb / 1e3),
+                        "bwd_tflops": 6.0 * n ** 3 * b / (ms_b / 1e3) / 1e12}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -374,6 +412,7 @@ def run_ours(args):
     batched = None
     if not args.no_batched:
         batched = run_batched(args, dev, world)
+    backward = None if args.no_batched else run_backward(args, dev)
 
     if rank != 0:
         return 0
@@ -428,6 +467,7 @@ def run_ours(args):
         "stages_ms": stats["ms_stage"], "sweeps": stats["sweeps"],
         "sweeps_stage1": stats["sweeps_stage1"], "off_T0": stats["off_T0"],
         "accuracy_mp": acc_mp, "plain": plain, "batched": batched,
+        "backward": backward,
         "kernels_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
     }
     print(json.dumps(line), flush=True)

@@ -165,6 +165,22 @@ int mpj_syevj_batched(mpj_batch_plan* plan, const double* A, double* Lambda, dou
 void mpj_batch_plan_destroy(mpj_batch_plan* plan);
 
 /* ------------------------------------------------------------------------
+ * Reverse-mode derivative of A = V diag(Lambda) V^T for a batch of `batch`
+ * symmetric n x n matrices (no counterpart in the paper; it lets training code
+ * differentiate through the solver):
+ *   A_bar = V (diag(Lambda_bar) + sym(F o (V^T V_bar))) V^T,
+ *   F_ij = 1/(lambda_j - lambda_i) (i != j; a zero gap contributes 0),
+ *   sym(X) = (X + X^T)/2; A_bar is exactly symmetric.
+ * Layouts (device): Lambda, gLambda: batch x n; V, gV, gA: batch x (n x n)
+ * column-major, ld n, contiguous.  gLambda or gV may be NULL (zero).  The
+ * derivative is well defined only for distinct eigenvalues.
+ * ------------------------------------------------------------------------ */
+int mpj_syev_backward_batched(const double* Lambda, const double* V, const double* gLambda,
+                              const double* gV, int n, int batch, double* gA,
+                              void* work, size_t work_bytes, void* stream);
+size_t mpj_syev_backward_workspace_bytes(int n, int batch);
+
+/* ------------------------------------------------------------------------
  * Single steps of the pipeline, exposed for stage-wise checks.
  * ------------------------------------------------------------------------ */
 

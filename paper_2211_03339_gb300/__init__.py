@@ -41,7 +41,8 @@ EXPORTS = ["mpj_syevj_mp", "mpj_syevj_plain", "mpj_syevj_workspace_bytes",
            "mpj_profile_enable", "mpj_profile_reset", "mpj_profile_read", "mpj_profile_name",
            "mpj_profile_classes", "mpj_kernel_launches",
            "mpj_batch_plan_create", "mpj_batch_plan_info", "mpj_syevj_batched",
-           "mpj_batch_plan_destroy",
+           "mpj_batch_plan_destroy", "mpj_syev_backward_batched",
+           "mpj_syev_backward_workspace_bytes",
            "mpj_status_string", "mpj_last_error", "mpj_version"]
 
 
@@ -133,6 +134,10 @@ def lib():
         L.mpj_batch_plan_info.restype = i
         L.mpj_syevj_batched.argtypes = [p, p, p, p, d, p, p, p]; L.mpj_syevj_batched.restype = i
         L.mpj_batch_plan_destroy.argtypes = [p]; L.mpj_batch_plan_destroy.restype = None
+        L.mpj_syev_backward_batched.argtypes = [p, p, p, p, i, i, p, p, sz, p]
+        L.mpj_syev_backward_batched.restype = i
+        L.mpj_syev_backward_workspace_bytes.argtypes = [i, i]
+        L.mpj_syev_backward_workspace_bytes.restype = sz
         _lib = L
         return L
 
@@ -388,3 +393,75 @@ def pack_symmetric(mats):
     """Concatenate column-major copies of square float64 numpy matrices."""
     import numpy as np
     return np.concatenate([np.asarray(M, dtype=np.float64).ravel(order="F") for M in mats])
+
+
+# ---------------------------------------------------------------- differentiation
+def syev_backward(lam, V, glam, gV):
+    """A_bar of a batch (b, n, n): V, gV are the logical matrices (b, n, n)."""
+    torch = _torch()
+    b, n = lam.shape
+    Vc = V.transpose(-1, -2).contiguous()               # column-major buffers
+    gVc = gV.transpose(-1, -2).contiguous() if gV is not None else None
+    gl = glam.contiguous() if glam is not None else None
+    gA = torch.empty((b, n, n), dtype=torch.float64, device=V.device)
+    ws = _workspace(lib().mpj_syev_backward_workspace_bytes(n, b), V.device)
+    rc = lib().mpj_syev_backward_batched(_ptr(lam.contiguous()), _ptr(Vc),
+                                         _ptr(gl) if gl is not None else None,
+                                         _ptr(gVc) if gVc is not None else None, n, b, _ptr(gA),
+                                         _ptr(ws), ws.numel(), _stream_ptr(V.device))
+    _check(rc, "mpj_syev_backward_batched")
+    return gA.transpose(-1, -2)                         # symmetric: either layout
+
+
+_plans = {}
+
+
+def _eigh_batched_forward(A, method):
+    b, n, _ = A.shape
+    key = (n, b, method, A.device.index)
+    plan = _plans.get(key)
+    if plan is None:
+        plan = _plans[key] = BatchPlan([n] * b, method=method)
+    Ac = A.transpose(-1, -2).contiguous().reshape(-1)   # column-major packed
+    Lam, V, st, sw = plan.outputs(A.device)
+    plan.run(Ac, Lam, V, st, sw)
+    if int((st != 0).sum().item()) != 0:
+        raise MPJError(int(st[st != 0][0].item()), "mpj_syevj_batched")
+    return Lam.view(b, n), V.view(b, n, n).transpose(-1, -2)
+
+
+def _make_function():
+    torch = _torch()
+
+    class EighFunction(torch.autograd.Function):
+        """Batched symmetric eigendecomposition (Alg. 4.1 forward) with the
+        hand-written backward kernel."""
+
+        @staticmethod
+        def forward(ctx, A, method="mp"):
+            lam, V = _eigh_batched_forward(A, method)
+            ctx.save_for_backward(lam, V)
+            return lam, V
+
+        @staticmethod
+        def backward(ctx, glam, gV):
+            lam, V = ctx.saved_tensors
+            return syev_backward(lam, V, glam, gV), None
+
+    return EighFunction
+
+
+_EighFunction = None
+
+
+def eigh(A, method="mp"):
+    """Differentiable (lambda ascending, V) of a batch (b, n, n) of symmetric float64
+    CUDA matrices, n <= 256: forward by the batched solver, backward by
+    mpj_syev_backward_batched."""
+    global _EighFunction
+    if _EighFunction is None:
+        _EighFunction = _make_function()
+    if A.dim() == 2:
+        lam, V = _EighFunction.apply(A.unsqueeze(0), method)
+        return lam[0], V[0]
+    return _EighFunction.apply(A, method)

@@ -17,8 +17,11 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(kThreads)
 k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda,
         const double* __restrict__ B, int ldb, double beta, double* __restrict__ C, int ldc,
-        int upper_mirror) {
+        int upper_mirror, long long sA, long long sB, long long sC) {
     const int bm = blockIdx.x, bn = blockIdx.y;
+    A += (size_t)blockIdx.z * sA;                     // batch (grid.z) strides
+    B += (size_t)blockIdx.z * sB;
+    C += (size_t)blockIdx.z * sC;
     if (upper_mirror && bm > bn) return;
     __shared__ __align__(16) double As[GK][GT + 2];   // As[k][m] = op(A)[m][k]
     __shared__ __align__(16) double Bs[GK][GT + 2];   // Bs[k][n] = op(B)[k][n]
@@ -78,23 +81,30 @@ k_dgemm(int M, int N, int K, double alpha, const double* __restrict__ A, int lda
     }
 }
 
-int dgemm(bool transA, bool transB, int M, int N, int K, double alpha, const double* A, int lda,
-          const double* B, int ldb, double beta, double* C, int ldc, bool upper_mirror,
-          cudaStream_t s) {
-    if (M <= 0 || N <= 0) return MPJ_SUCCESS;
-    dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT);
+int dgemm_batched(bool transA, bool transB, int M, int N, int K, double alpha, const double* A,
+                  int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                  double* C, int ldc, long long sC, int batch, bool upper_mirror, cudaStream_t s) {
+    if (M <= 0 || N <= 0 || batch <= 0) return MPJ_SUCCESS;
+    dim3 grid((M + GT - 1) / GT, (N + GT - 1) / GT, batch);
     int um = upper_mirror ? 1 : 0;
     MPJ_PROF(PC_DGEMM, s);
     if (!transA && !transB)
-        k_dgemm<false, false><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um);
+        k_dgemm<false, false><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um, sA, sB, sC);
     else if (transA && !transB)
-        k_dgemm<true, false><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um);
+        k_dgemm<true, false><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um, sA, sB, sC);
     else if (!transA && transB)
-        k_dgemm<false, true><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um);
+        k_dgemm<false, true><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um, sA, sB, sC);
     else
-        k_dgemm<true, true><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um);
+        k_dgemm<true, true><<<grid, kThreads, 0, s>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, um, sA, sB, sC);
     MPJ_LAUNCH_CHECK("k_dgemm");
     return MPJ_SUCCESS;
+}
+
+int dgemm(bool transA, bool transB, int M, int N, int K, double alpha, const double* A, int lda,
+          const double* B, int ldb, double beta, double* C, int ldc, bool upper_mirror,
+          cudaStream_t s) {
+    return dgemm_batched(transA, transB, M, N, K, alpha, A, lda, 0, B, ldb, 0, beta, C, ldc, 0, 1,
+                         upper_mirror, s);
 }
 
 }  // namespace mpj

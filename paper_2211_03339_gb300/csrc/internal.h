@@ -118,6 +118,10 @@ int dgemm(bool transA, bool transB, int M, int N, int K, double alpha, const dou
           const double* B, int ldb, double beta, double* C, int ldc, bool upper_mirror,
           cudaStream_t s);
 
+int dgemm_batched(bool transA, bool transB, int M, int N, int K, double alpha, const double* A,
+                  int lda, long long sA, const double* B, int ldb, long long sB, double beta,
+                  double* C, int ldc, long long sC, int batch, bool upper_mirror, cudaStream_t s);
+
 // Blocked MGS (Lemma 2.1) in place on Q (m x n, ld = ldq).  Needs n x 32 doubles
 // of workspace for the panel projections.
 size_t mgs_workspace_bytes(int m, int n);

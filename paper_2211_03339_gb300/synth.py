@@ -11,7 +11,8 @@ here, so the matrices below are stand-ins with the same structure:
 * ``A = Q diag(lam) Q^T`` with a Haar-distributed orthogonal ``Q`` (QR of a
   standard Gaussian matrix, columns signed so that ``diag(R) > 0``), made
   exactly symmetric by ``(A + A^T)/2``;
-* spectra: ``uniform`` in [-1, 1]; ``geometric`` with ``|lam_i| =
+* spectra: ``uniform`` in [-1, 1]; ``gapped`` (uniform in [-1, 1], one eigenvalue per
+  stratum of width 2/n, so the minimum gap is at least 0.8/n); ``geometric`` with ``|lam_i| =
   10^(-8 (i-1)/(n-1))`` and random signs; ``cluster``: 10 centres in
   ``linspace(-0.9, 0.9, 10)``, members uniform in ``centre +- 5e-7``;
   and the Example 1 modes 3/4/5 (geometric, arithmetic, log-uniform with
@@ -25,7 +26,7 @@ from __future__ import annotations
 
 import numpy as np
 
-SPECTRA = ("uniform", "geometric", "cluster", "mode3", "mode4", "mode5")
+SPECTRA = ("uniform", "geometric", "cluster", "mode3", "mode4", "mode5", "gapped")
 
 
 def seed_for(config_id: int, index: int) -> int:
@@ -56,6 +57,9 @@ def spectrum(kind: str, n: int, rng: np.random.Generator, kappa: float = 1e6) ->
         centres = np.linspace(-0.9, 0.9, 10)
         per = -(-n // 10)
         lam = np.concatenate([c + rng.uniform(-5e-7, 5e-7, per) for c in centres])[:n]
+    elif kind == "gapped":     # uniform in [-1, 1], stratified: min gap >= 0.4 * 2/n (>= 1e-3 for n <= 800)
+        h = 2.0 / n
+        lam = -1.0 + h * (np.arange(n) + 0.5 + rng.uniform(-0.3, 0.3, n))
     elif kind == "mode3":      # geometric, lam_1 = 1 ... lam_n = 1/kappa
         e = np.arange(n) / max(n - 1, 1)
         lam = kappa ** (-e)
