@@ -73,6 +73,39 @@ def spectrum(kind: str, n: int, rng: np.random.Generator, kappa: float = 1e6) ->
     return np.asarray(lam, dtype=np.float64)
 
 
+def multiple_spectrum(s: int, r: int, mode: int, kappa: float, rng: np.random.Generator) -> np.ndarray:
+    """Example 2: lam (length s) repeated r times (lam kron 1_r), modes 1-5.
+
+    Modes 1, 2 and 4 follow the stated formulas.  The printed modes 3 and 5
+    (kappa .* linspace(-1, 0, s) and kappa .* (-rand(s, 1))) would give a
+    non-positive-definite A, contradicting the example's own statement; they are
+    read as kappa .^ linspace(-1, 0, s) and kappa .^ (-rand(s, 1)) (geometric and
+    log-uniform in [1/kappa, 1])."""
+    if mode == 1:
+        lam = np.concatenate([[1.0], np.ones(s - 1) / kappa])
+    elif mode == 2:
+        lam = np.concatenate([np.ones(s - 1), [1.0 / kappa]])
+    elif mode == 3:
+        lam = kappa ** np.linspace(-1.0, 0.0, s)
+    elif mode == 4:
+        lam = 1.0 - (1.0 - 1.0 / kappa) * np.linspace(0.0, 1.0, s)
+    elif mode == 5:
+        lam = kappa ** (-rng.uniform(0.0, 1.0, s))
+    else:
+        raise ValueError("mode must be 1..5")
+    return np.kron(lam, np.ones(r))
+
+
+def sym_matrix_multiple(r: int, s: int, mode: int, kappa: float = 1e4, seed: int = 0):
+    """Example 2 stand-in: A = P diag(lam kron 1_r) P^T, n = r s, Haar P."""
+    rng = rng_for(seed)
+    lam = multiple_spectrum(s, r, mode, kappa, rng)
+    P = haar(rng, r * s)
+    A = (P * lam[None, :]) @ P.T
+    A = 0.5 * (A + A.T)
+    return np.asfortranarray(A), np.sort(lam)
+
+
 def sym_matrix(n: int, kind: str = "uniform", seed: int = 0, kappa: float = 1e6):
     """Return (A, lam_sorted_ascending) with A = Q diag(lam) Q^T, column-major."""
     rng = rng_for(seed)

@@ -244,3 +244,46 @@ def test_gesvj_full_size_properties(mpj):
     assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
     assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
     assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
+
+
+# ------------------------------------------------------------------ multiple eigenvalues (Example 2)
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5])
+def test_syevj_multiple_eigenvalues(mpj, mode):
+    """Example 2 stand-in, (r, s) = (4, 128): eigenvalues of multiplicity 4.  Within a
+    multiple eigenvalue only the invariant subspace is unique, so the checks are the
+    residual, orthogonality and eigenvalues (against the exact spectrum)."""
+    r, s = 4, 128
+    n = r * s
+    A, lam = synth.sym_matrix_multiple(r, s, mode, kappa=1e4, seed=synth.seed_for(4, mode))
+    for f in (mpj.syevj_mp, mpj.syevj_plain):
+        L, V, st = f(dev(A))
+        L, V = host(L), host(V)
+        res, orth = evd_metrics(A, L, V)
+        assert res <= 10 * n * U and orth <= 10 * n * U, (f.__name__, res, orth)
+        assert np.abs(L - lam).max() <= 14 * n * U * np.abs(lam).max()
+
+
+def test_syevj_mp_n8192_properties(mpj):
+    """Largest single-matrix size of the workload (n = 8192), preconditioned path."""
+    n = 8192
+    A, lam = synth.sym_matrix(n, "uniform", seed=synth.seed_for(1, n))
+    Ad = dev(A)
+    Lg, Vg, st = mpj.syevj_mp(Ad)
+    Vt = Vg.contiguous()
+    R = Ad @ Vt - Vt * Lg[None, :]
+    res = (torch.linalg.matrix_norm(R) / torch.linalg.matrix_norm(Ad)).item()
+    orth = torch.linalg.matrix_norm(Vt.T @ Vt - torch.eye(n, dtype=torch.float64, device="cuda")).item()
+    assert res <= 10 * n * U and orth <= 10 * n * U
+    a2 = np.abs(lam).max()
+    assert np.abs(host(Lg) - lam).max() <= 14 * n * U * a2
+
+
+def test_gesvj_8192x1024_properties(mpj):
+    m, n = 8192, 1024
+    A, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, 1), sigma_min=1e-10)
+    Sg, Ug, Vg, st = mpj.gesvj_mp(dev(A))
+    Sg, Ug, Vg = host(Sg), host(Ug), host(Vg)
+    assert np.abs(Sg - sig).max() <= 10 * n * U * sig[0] + 4 * n * U * sig[0]
+    assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
+    assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
+    assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
