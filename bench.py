@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--batch", type=int, default=10000, help="matrices in the batched workload")
     ap.add_argument("--once", action="store_true",
                     help="run one mpj_syevj_mp solve and exit (for profiler captures)")
+    ap.add_argument("--study", choices=["ex2", "svd", "precision"],
+                    help="print one JSON line per case of a sweep-count study instead of the "
+                         "benchmark line: ex2 = multiple eigenvalues (Example 2, n = 2048/4096, "
+                         "r = 4); svd = Alg. 5.2 vs 5.1 at 4096x2048 and 8192x1024; precision = "
+                         "FP64 sweeps vs the accuracy of stage 1 (Example 2)")
     return ap.parse_args()
 
 
@@ -487,10 +492,130 @@ def run_once(args):
     return 0
 
 
+def _gpu_metrics(A, L, V):
+    """Res and OR-P as defined for the tables of Sec. 6 (OR-P with the 1/sqrt(n))."""
+    import torch
+    n = A.shape[0]
+    R = A @ V - V * L[None, :]
+    res = (torch.linalg.matrix_norm(R) / torch.linalg.matrix_norm(A)).item()
+    orth = torch.linalg.matrix_norm(V.T @ V - torch.eye(n, dtype=V.dtype, device=V.device)).item()
+    return res, orth
+
+
+def study_ex2(args):
+    """Example 2 (A = P diag(lam kron 1_r) P^T, r = 4) at n = 2048 and 4096: the
+    quantities of the Example 2 tables (off(Q^T A Q), d(A)/4, Res, OR-P, CT-Pre,
+    CT-J, SP) for the GPU Alg. 4.1."""
+    import numpy as np
+    import torch
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import synth
+    r = 4
+    for n in (2048, 4096):
+        s = n // r
+        for kappa in (1e3, 1e6):
+            for mode in (1, 2, 3, 4, 5):
+                A_np, lam = synth.sym_matrix_multiple(r, s, mode, kappa, seed=synth.seed_for(4, 100 * mode + int(np.log10(kappa))))
+                distinct = np.unique(lam)
+                d4 = float(np.min(np.diff(distinct))) / 4 if len(distinct) > 1 else float("inf")
+                A = torch.from_numpy(A_np).cuda()
+                mpj.syevj_mp(A)                                   # warm-up (workspace, caches)
+                torch.cuda.synchronize()
+                L, V, st = mpj.syevj_mp(A)
+                torch.cuda.synchronize()
+                res, orth = _gpu_metrics(A, L, V)
+                lam_err = float(np.max(np.abs(L.cpu().numpy() - lam)))
+                print(json.dumps({"study": "ex2", "n": n, "r": r, "mode": mode, "kappa": kappa,
+                                  "off_QtAQ": st["off_T0"], "d_over_4": d4, "Res": res,
+                                  "OR_P": orth / np.sqrt(n), "CT_pre_s": sum(st["ms_stage"][:3]) / 1e3,
+                                  "CT_J_s": st["ms_stage"][3] / 1e3, "SP": st["sweeps"],
+                                  "SP_stage1": st["sweeps_stage1"], "lam_err_over_nu": lam_err / (n * U),
+                                  "res_over_nu": res / (n * U), "orth_over_nu": orth / (n * U)}), flush=True)
+    return 0
+
+
+def study_svd(args):
+    """Alg. 5.2 against Alg. 5.1 on the SVD workloads (sigma geometric 1 .. 1e-10, and
+    1 .. 1e-6 for the condition numbers of the SVD tables)."""
+    import numpy as np
+    import torch
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import synth
+    for (m, n, idx) in ((4096, 2048, 0), (8192, 1024, 1)):
+        for smin in (1e-10, 1e-6):
+            A_np, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, idx), sigma_min=smin)
+            A = torch.from_numpy(A_np).cuda()
+            for name, f in (("mp", mpj.gesvj_mp), ("plain", mpj.gesvj_plain)):
+                opts = mpj.Options(max_sweeps=80)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                S, Uo, V, st = f(A, options=opts)
+                torch.cuda.synchronize()
+                wall = time.perf_counter() - t0
+                I = torch.eye(n, dtype=torch.float64, device=A.device)
+                res = (torch.linalg.matrix_norm(A @ V - Uo * S[None, :]) / torch.linalg.matrix_norm(A)).item()
+                oru = torch.linalg.matrix_norm(Uo.T @ Uo - I).item()
+                orv = torch.linalg.matrix_norm(V.T @ V - I).item()
+                Sn = S.cpu().numpy()
+                print(json.dumps({"study": "svd", "m": m, "n": n, "sigma_min": smin, "method": name,
+                                  "s": wall, "sweeps": st["sweeps"], "sweeps_stage1": st["sweeps_stage1"],
+                                  "JU_over_N": st["rotations"], "JU1_over_N": st["rotations_stage1"],
+                                  "ms_stage": st["ms_stage"],
+                                  "sigma_abs_err_over_nu_s1": float(np.max(np.abs(Sn - sig))) / (n * U * sig[0]),
+                                  "sigma_rel_err_max": float(np.max(np.abs(Sn - sig) / sig)),
+                                  "res_over_nu": res / (n * U), "orthU_over_nu": oru / (n * U),
+                                  "orthV_over_nu": orv / (n * U)}), flush=True)
+    return 0
+
+
+def _round_significand(A, p):
+    """A with every entry rounded to p significant bits (round to nearest even)."""
+    import torch
+    mant, expo = torch.frexp(A)                   # A = mant * 2^expo, 0.5 <= |mant| < 1
+    return torch.ldexp(torch.round(torch.ldexp(mant, torch.full_like(expo, p))),
+                       expo - p)
+
+
+def study_precision(args):
+    """Off-norm of T after each FP64 sweep for stage-1 accuracies 2^-p (Example 2,
+    n = 2048, r = 4, kappa = 1e6): stage 1 sees A rounded to p significant bits and
+    stops at ||off|| <= 2^-p ||A||_F (its arithmetic stays FP32); steps 2-4 use A."""
+    import numpy as np
+    import torch
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import synth
+    n, r = 2048, 4
+    for mode in (3, 4, 5):
+        A_np, lam = synth.sym_matrix_multiple(r, n // r, mode, 1e6, seed=synth.seed_for(4, 500 + mode))
+        A = torch.from_numpy(A_np).cuda()
+        normA = torch.linalg.matrix_norm(A).item()
+        for p in (8, 11, 16, 24):
+            Ap = _round_significand(A, p) if p < 24 else A
+            Z, _, st1 = mpj.stage1_syevj32(Ap, options=mpj.Options(tol_stage1=2.0 ** -p))
+            Q = mpj.mgs(Z)
+            T = mpj.congruence(A, Q)
+            offs = [torch.linalg.matrix_norm(T - torch.diag(torch.diagonal(T))).item()]
+            P = Q
+            for j in range(40):
+                T, P, st = mpj.sweeps(T, P, normA=normA, options=mpj.Options(max_sweeps=1),
+                                      allow_not_converged=True)
+                offs.append(st["off_final"])
+                if st["status"] == 0:
+                    break
+            print(json.dumps({"study": "precision", "n": n, "r": r, "mode": mode, "kappa": 1e6,
+                              "p_bits": p, "stage1_sweeps": st1["sweeps_stage1"],
+                              "off_after_sweep": offs, "fp64_sweeps": len(offs) - 1}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.once:
         return run_once(args)
+    if args.study:
+        import __graft_entry__
+        __graft_entry__.build()
+        return {"ex2": study_ex2, "svd": study_svd, "precision": study_precision}[args.study](args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -79,6 +79,8 @@ struct ProfScope {
     ~ProfScope();
 };
 void prof_flush();
+// Per-sweep trace on stderr (rotation counts, off-norms) when MPJ_TRACE is set.
+bool trace_on();
 #define MPJ_PROF(cls, stream) ::mpj::ProfScope _mpj_prof_scope((cls), (stream))
 
 // ---------------------------------------------------------------- shapes

@@ -13,6 +13,8 @@
 //   k_apply1  C[:, IJ] = C[:, IJ] W and V[:, IJ] = V[:, IJ] W, 64-row slabs.
 // The number of applied rotations is read back once per sweep (Sec. 6 stop rule).
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 
 #include "internal.h"
 #include "jacobi_device.cuh"
@@ -236,6 +238,16 @@ static int launch_round1(Real* C, int ldc, Real* V, int m, int N, Real* Wbuf, Re
     return MPJ_SUCCESS;
 }
 
+// Fraction of N below which a sweep's rotation count turns the compensated
+// Gram on (0: only once a sweep passes the stopping rule).  MPJ_GRAM_COMP_SWITCH
+// overrides it (a negative value disables compensation); used to compare the
+// schedules on the same inputs.
+constexpr double kCompSwitch = 0.0;
+static double comp_switch_override(double dflt) {
+    const char* e = std::getenv("MPJ_GRAM_COMP_SWITCH");
+    return e ? atof(e) : dflt;
+}
+
 template <class Real>
 int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, double tol_rot,
                     double ju_ratio, int max_sweeps, int max_inner, void* work, cudaStream_t s,
@@ -261,9 +273,17 @@ int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, doubl
     res->status = MPJ_NOT_CONVERGED;
     const int rounds = 2 * K - 1;
     const Real gate = (Real)(sizeof(Real) == 8 ? 1.0 / 67108864.0 : 1.0 / 4096.0);   // 2^-26 / 2^-12
-    // The compensated (Dot2) Gram is switched on once a sweep applies fewer than
-    // N rotations: the cosines that decide convergence (and the orthogonality of
-    // U) are then accurate to working precision instead of sqrt(m) ulps.
+    // FP64 only: the compensated (Dot2) Gram makes the cosines that decide
+    // convergence (and the orthogonality of U) accurate to working precision
+    // whatever the growth of the partial sums, at about four times the cost of
+    // an uncompensated sweep.  By default the sweeps run uncompensated until one
+    // passes the stopping rule; then compensated sweeps continue until one
+    // passes it again, so the final decision rests on cosines accurate to
+    // working precision (comp_switch > 0 turns compensation on earlier, once a
+    // sweep applies fewer than comp_switch * N rotations; comp_switch < 0
+    // never, the first sweep that passes the rule ends the iteration).
+    const bool dbl = sizeof(Real) == 8;
+    const double comp_switch = dbl ? comp_switch_override(kCompSwitch) : -1.0;
     int comp = 0;
     while (res->sweeps < max_sweeps) {
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
@@ -281,8 +301,13 @@ int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, doubl
         prof_flush();
         res->sweeps += 1;
         res->rotations += (double)hs.u[0];
-        if (hs.u[0] == 0 || (double)hs.u[0] < ju_ratio * Npairs) { res->status = MPJ_SUCCESS; break; }
-        if (sizeof(Real) == 8 && (double)hs.u[0] < Npairs) comp = 1;
+        if (trace_on())
+            fprintf(stderr, "[mpj] onesided<%s> m=%d n=%d sweep %d: %llu rotations (%.4f N) comp=%d\n",
+                    dbl ? "f64" : "f32", m, n, res->sweeps, hs.u[0], hs.u[0] / Npairs, comp);
+        const double applied = (double)hs.u[0];
+        const bool rule = hs.u[0] == 0 || applied < ju_ratio * Npairs;
+        if (rule && (comp || comp_switch < 0.0)) { res->status = MPJ_SUCCESS; break; }
+        if (!comp && comp_switch >= 0.0 && (rule || applied < comp_switch * Npairs)) comp = 1;
     }
     return MPJ_SUCCESS;
 }

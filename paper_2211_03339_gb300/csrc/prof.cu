@@ -1,6 +1,7 @@
 // prof.cu -- per-kernel-class launch counters and optional CUDA-event timing
 // of every launch on the stream it is launched on (diagnostics for the
 // roofline report; no effect on results).
+#include <cstdlib>
 #include <mutex>
 #include <vector>
 
@@ -62,6 +63,14 @@ void prof_flush() {
     }
     g_pending.swap(keep);
     cudaGetLastError();   // cudaEventQuery's cudaErrorNotReady is not an error of ours
+}
+
+bool trace_on() {
+    static const bool on = [] {
+        const char* e = std::getenv("MPJ_TRACE");
+        return e && *e && *e != '0';
+    }();
+    return on;
 }
 
 }  // namespace mpj

@@ -179,6 +179,9 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
         off = sqrt(hs.d[0]);
         res->sweeps += 1;
         res->rotations += (double)hs.u[0];
+        if (trace_on())
+            fprintf(stderr, "[mpj] twosided<%s> n=%d sweep %d: %llu rotations, off %.3e\n",
+                    dbl ? "f64" : "f32", n, res->sweeps, hs.u[0], ldexp(off, -e2));
         if (hs.u[0] == 0) { res->status = MPJ_SUCCESS; break; }
     }
     if (res->status == MPJ_NOT_CONVERGED && std::isfinite(off) && !(off > tol_abs))
