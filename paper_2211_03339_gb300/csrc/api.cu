@@ -116,7 +116,8 @@ struct EvdBufs {
 };
 
 size_t evd_engine_bytes(int N, int B) {
-    return max2(twosided_workspace_bytes<double>(N, B), twosided_workspace_bytes<float>(N, B));
+    size_t e = max2(twosided_workspace_bytes<double>(N, B), twosided_workspace_bytes<float>(N, B));
+    return B == 32 ? max2(e, tc32_workspace_bytes(N)) : e;
 }
 
 int evd_layout(Arena& a, int n, int N, int B, bool mp, EvdBufs& b) {
@@ -149,11 +150,23 @@ int stage1_evd(const double* A, int lda, int n, int N, int B, double normA, cons
                EvdBufs& b, SweepResult* r1, cudaStream_t s) {
     MPJ_TRY(copy_pad_f32(A, lda, n, n, b.T32, N, N, N, false, s));
     MPJ_TRY(set_identity_f32(b.V32, N, N, N, s));
-    MPJ_TRY(twosided_sweeps<float>(b.T32, b.V32, N, n, B, op.tol1 * normA, kUps, op.max_sweeps1,
-                                   op.max_inner, b.eng, s, r1));
+    const bool tc = B == 32 && tc_enabled();
+    if (tc) {
+        // tensor-core engine: V32 holds V row-major; the FP64 T buffer (unused until
+        // step 3) is the scratch P of its two passes
+        MPJ_TRY(twosided_sweeps_tc32(b.T32, b.V32, reinterpret_cast<float*>(b.T64), N, n,
+                                     op.tol1 * normA, kUps, op.max_sweeps1, op.max_inner, b.eng, s, r1));
+    } else {
+        MPJ_TRY(twosided_sweeps<float>(b.T32, b.V32, N, n, B, op.tol1 * normA, kUps, op.max_sweeps1,
+                                       op.max_inner, b.eng, s, r1));
+    }
     MPJ_TRY(diag_to_f64(b.T32, false, N, n, b.sc.d, s));
     MPJ_TRY(rank_sort(b.sc.d, 1, n, false, b.sc.perm, s));
-    MPJ_TRY(gather_z32(b.V32, N, b.sc.perm, n, b.Q, n, s));
+    if (tc) {
+        MPJ_TRY(gather_z32_rowmajor(b.V32, N, b.sc.perm, n, b.Q, n, s));
+    } else {
+        MPJ_TRY(gather_z32(b.V32, N, b.sc.perm, n, b.Q, n, s));
+    }
     return MPJ_SUCCESS;
 }
 

@@ -37,11 +37,15 @@ struct ApplySmem {
 };
 
 // Block-pair solve.  smem: InnerLayout<Real, 2B>::bytes.  Returns the number of
-// rotations applied (all threads).  Fout: M*M row-major F of this pair.
-template <class Real, int B>
+// rotations applied (all threads).  Fout: M*M row-major F of this pair.  With
+// WriteBack the rotated 2b x 2b block is stored back to T; without it T is left
+// as it was and the rotated block goes to Sout (M*M row-major) instead (the
+// tensor-core engine applies W to the whole of T and then puts the solver's
+// block, with its exact zeros, in place of the recomputed diagonal block).
+template <class Real, int B, bool WriteBack = true>
 __device__ int pair_solve(Real* __restrict__ T, int N, int round, int pair, Real eps, Real tau,
                           Real gate, int max_inner, Real* __restrict__ Fout, float* fmax_out,
-                          unsigned char* smraw) {
+                          unsigned char* smraw, Real* __restrict__ Sout = nullptr) {
     constexpr int M = 2 * B;
     constexpr int LD = M + 1;
     Real* S = reinterpret_cast<Real*>(smraw);
@@ -60,9 +64,16 @@ __device__ int pair_solve(Real* __restrict__ T, int N, int round, int pair, Real
     }
     __syncthreads();
     int applied = inner_jacobi<Real, M>(S, F, cs, ip, eps, tau, max_inner);
-    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
-        int r = t % M, c = t / M;
-        T[(size_t)pair_global(r, I, J, B) + (size_t)pair_global(c, I, J, B) * N] = S[c * LD + r];
+    if (WriteBack) {
+        for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+            int r = t % M, c = t / M;
+            T[(size_t)pair_global(r, I, J, B) + (size_t)pair_global(c, I, J, B) * N] = S[c * LD + r];
+        }
+    } else if (Sout) {
+        for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+            int c = t % M, r = t / M;
+            Sout[t] = S[c * LD + r];                 // row-major: Sout[r*M + c]
+        }
     }
     finish_block<Real, M>(F, G, Fout, gate, flag, fmax_out);
     __syncthreads();

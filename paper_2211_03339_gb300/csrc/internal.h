@@ -69,7 +69,8 @@ struct HostScratch {
 enum ProfClass {
     PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
-    PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, kProfClasses
+    PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2V_F32,
+    kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -103,6 +104,19 @@ size_t twosided_workspace_bytes(int N, int B);
 template <class Real>
 int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, double eps_skip,
                     int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res);
+
+// The FP32 engine of step 1 with the rotations applied on the tensor cores
+// (tc_apply.cu): block size b = 32 (N a multiple of 64), T and P column-major
+// N x N (P: scratch of N^2 floats), Vt = V^T column-major (V row-major).
+size_t tc32_workspace_bytes(int N);
+int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol_abs,
+                         double eps_skip, int max_sweeps, int max_inner, void* work, cudaStream_t s,
+                         SweepResult* res);
+// Z[:, c] = V[:, perm[c]] (widened) from a row-major V.
+int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double* Z, int ldz,
+                        cudaStream_t s);
+// The tensor-core engine is used for b = 32 unless MPJ_TC=0 (comparison switch).
+bool tc_enabled();
 
 // One-sided block Jacobi (Alg. 5.1 / steps 4-10 of Alg. 5.2) on C (m x N, ld = ldc)
 // and V (N x N, ld = N).

@@ -1,0 +1,429 @@
+// tc_apply.cu -- the FP32 block Jacobi of step 1 of Algorithm 4.1 with the
+// rotation application on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// A round of the parallel order replaces T by W^T T W and V by V W, where W is
+// block diagonal over the disjoint block pairs (I, J) of the round (one 2b x 2b
+// orthogonal block W_b = I + F_b per pair, from the block-pair solves).  Both
+// are written as right multiplications of 128-row slabs by W_b:
+//
+//   pass 1   P = T W          P[rows, IJ_b] = T[rows, IJ_b] + T[rows, IJ_b] F_b
+//   pass 2   T' = P^T W       (= W^T T W, as T is symmetric), and V' = V W
+//
+// Every tile is one 128 x 64 x 64 product on the tensor cores in delta form
+// (X + X F), with X and F split into TF32 pairs (hi + lo) and the three
+// products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM, which carries
+// about 21 bits of each product -- the accuracy of the FP32 SIMT products it
+// replaces.  The operand X must be K-major (the 64 columns of the pair
+// contiguous for each row): T is read through its transpose (T and P are
+// column-major, so T^T[rows, IJ_b] is contiguous along IJ_b), and V is kept
+// row-major (Vt = V^T column-major).  Pass 1 and pass 2 write column-major
+// (each warp stores 32 consecutive rows of one column); V is written row-major
+// through a shared-memory staging tile.
+//
+// Traffic per round: T and P are read and written once each, V read and written
+// once: 6 N^2 floats.  The block-pair solves are the FP32 k_solve2 kernels of
+// the SIMT engine, without writing the rotated block back (pass 1 and 2 rotate
+// the diagonal blocks too).
+#include <cmath>
+#include <cstdio>
+
+#include <cuda.h>
+
+#include "internal.h"
+#include "engine_device.cuh"
+#include "tc_device.cuh"
+
+namespace mpj {
+
+namespace {
+
+constexpr int kSlab = 128;          // rows of one tile = M of the MMA
+constexpr int kTcThreads = 128;     // warp w owns TMEM lanes 32w .. 32w+31 (rows)
+constexpr int kTcWait = 1 << 22;    // mbarrier polls before a tile gives up
+constexpr int kB = 32;              // block size b; pair width 2b = 64 = K = N of the MMA
+constexpr int kM = 2 * kB;
+
+
+__global__ void __launch_bounds__(kSolveThreads)
+k_solve2_nb(float* __restrict__ T, int N, float* __restrict__ Fbuf, float* __restrict__ Sbuf,
+            float* __restrict__ Fimg, float* __restrict__ fmax, int round, float eps, float tau,
+            float gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int applied = pair_solve<float, kB, false>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
+                                               Fbuf + (size_t)blockIdx.x * kM * kM,
+                                               fmax + blockIdx.x, smraw,
+                                               Sbuf + (size_t)blockIdx.x * kM * kM);
+    if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
+    // TF32 hi / lo image of F_b^T (row n, column k holds F_b[k][n]) for the pass
+    // kernel's B operand; the block's F is still in shared memory (after S).
+    const float* Fs = reinterpret_cast<const float*>(smraw) + kM * (kM + 1);
+    float* img = Fimg + (size_t)blockIdx.x * 2 * kM * kM;
+    for (int t = threadIdx.x; t < kM * kM; t += blockDim.x) {
+        const int n = t / kM, k = t % kM;
+        float h, l;
+        tc::split_tf32(Fs[n * (kM + 1) + k], h, l);
+        img[t] = h;
+        img[kM * kM + t] = l;
+    }
+}
+
+// Per-CTA shared memory of the pass kernel (offsets in floats from a 1024-byte
+// aligned base).  Two load slots, each: the two 32-column chunks of the X tile
+// (128 rows x 128 bytes, 128-byte swizzle, as the TMA writes them) and the
+// TF32 hi/lo image of F_b^T for the two K halves (64 rows x 128 bytes each).
+// Then the hi and lo TF32 parts of X in the same layout (MMA operand A).
+constexpr int kChunk = kSlab * 32;                   // floats of one X chunk (16 KB)
+constexpr int kFChunk = kM * 32;                     // floats of one F chunk (8 KB)
+constexpr int kSlotFloats = 2 * kChunk + 4 * kFChunk;
+constexpr int kXsplitOff = 2 * kSlotFloats;          // XhI, XhJ, XlI, XlJ
+constexpr size_t kPassSmem = sizeof(float) * (size_t)(kXsplitOff + 4 * kChunk) + 1024;
+constexpr uint32_t kSlotBytes = sizeof(float) * kSlotFloats;   // TMA bytes per item
+
+struct PassMaps {
+    CUtensorMap in_t;       // X source of the T tiles (T in pass 1, P in pass 2)
+    CUtensorMap v;          // Vt (row-major V), loads and stores
+    CUtensorMap f;          // F image: (pairs x 128) rows of 64 floats
+};
+
+// The item sequence of a CTA: it, it + gridDim.x, ...; V tiles whose W_b is the
+// identity are skipped (they are unchanged).
+__device__ __forceinline__ int next_item(int it, int total, int items_T, int n_slabs,
+                                         const float* __restrict__ fmax) {
+    while (it < total && it >= items_T && fmax[(it - items_T) / n_slabs] == 0.f) it += gridDim.x;
+    return it;
+}
+
+__device__ __forceinline__ void issue_item(const PassMaps& maps, int it, int items_T, int n_slabs,
+                                           int round, int nblocks, float* slot, uint64_t* full) {
+    const bool vt = it >= items_T;
+    const int item = vt ? it - items_T : it;
+    const int s = item % n_slabs, b = item / n_slabs;
+    int I, J;
+    round_pair(round, b, nblocks, I, J);
+    const CUtensorMap* mx = vt ? &maps.v : &maps.in_t;
+    tc::mbar_expect_tx(full, kSlotBytes);
+    tc::tma_load_2d(slot, mx, I * kB, s * kSlab, full);
+    tc::tma_load_2d(slot + kChunk, mx, J * kB, s * kSlab, full);
+    float* F = slot + 2 * kChunk;
+    tc::tma_load_2d(F, &maps.f, 0, b * 2 * kM, full);                      // hi, k < 32
+    tc::tma_load_2d(F + kFChunk, &maps.f, 32, b * 2 * kM, full);           // hi, k >= 32
+    tc::tma_load_2d(F + 2 * kFChunk, &maps.f, 0, b * 2 * kM + kM, full);   // lo, k < 32
+    tc::tma_load_2d(F + 3 * kFChunk, &maps.f, 32, b * 2 * kM + kM, full);  // lo, k >= 32
+}
+
+// Persistent pass kernel.  Items [0, items_T): Tout[rows, IJ_b] = X + X F_b with
+// X[m][k] = In[col(k) + (row0 + m) N] (In^T, K-major), written column-major;
+// with Sbuf the rows in IJ_b take the solver's rotated block instead.  Items
+// [items_T, total): the rows slab of the row-major V times W_b, stored back with
+// TMA.  Each CTA keeps two items in flight: the TMA loads of item k+2 are issued
+// as soon as item k has left its slot.
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N, int n_slabs,
+          int items_T, int total, const float* __restrict__ Sbuf, const float* __restrict__ fmax,
+          int round, unsigned long long* __restrict__ err) {
+    extern __shared__ unsigned char smraw[];
+    float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full[2];
+    __shared__ __align__(8) uint64_t mma_done;
+    __shared__ uint32_t tmem_slot;
+    float* Xh = sm + kXsplitOff;                     // XhI, XhJ
+    float* Xl = Xh + 2 * kChunk;                     // XlI, XlJ
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nblocks = N / kB;
+    if (tid == 0) {
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(&mma_done, 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kM);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    int it0 = next_item(blockIdx.x, total, items_T, n_slabs, fmax);
+    int it1 = it0 < total ? next_item(it0 + gridDim.x, total, items_T, n_slabs, fmax) : total;
+    if (tid == 0) {
+        if (it0 < total) issue_item(maps, it0, items_T, n_slabs, round, nblocks, sm, &full[0]);
+        if (it1 < total) issue_item(maps, it1, items_T, n_slabs, round, nblocks, sm + kSlotFloats, &full[1]);
+    }
+    bool ok = true;
+    int k = 0;
+    for (int it = it0; it < total; ++k) {
+        const int slot = k & 1;
+        float* sl = sm + slot * kSlotFloats;
+        const bool vt = it >= items_T;
+        const int item = vt ? it - items_T : it;
+        const int s = item % n_slabs, b = item / n_slabs;
+        int I, J;
+        round_pair(round, b, nblocks, I, J);
+        const int row0 = s * kSlab;
+        ok = tc::mbar_wait(&full[slot], (k >> 1) & 1, kTcWait) && ok;       // waited even after an error
+        // split X (same swizzled offsets in the source and in Xh / Xl)
+#pragma unroll 4
+        for (int i = tid; i < 2 * kChunk / 4; i += kTcThreads) {
+            const float4 x = reinterpret_cast<const float4*>(sl)[i];
+            float4 h, l;
+            tc::split_tf32(x.x, h.x, l.x);
+            tc::split_tf32(x.y, h.y, l.y);
+            tc::split_tf32(x.z, h.z, l.z);
+            tc::split_tf32(x.w, h.w, l.w);
+            reinterpret_cast<float4*>(Xh)[i] = h;
+            reinterpret_cast<float4*>(Xl)[i] = l;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0 && ok) {
+            constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, kSlab, kM);
+            const float* F = sl + 2 * kChunk;
+#pragma unroll
+            for (int ks = 0; ks < kM / 8; ++ks) {          // K = 8 per MMA, 32 bytes along the row
+                const int ch = ks >> 2;
+                const uint32_t off = (ks & 3) * 32;
+                const uint32_t xh = tc::smem_u32(Xh + ch * kChunk) + off;
+                const uint32_t xl = tc::smem_u32(Xl + ch * kChunk) + off;
+                const uint32_t fh = tc::smem_u32(F + ch * kFChunk) + off;
+                const uint32_t fl = tc::smem_u32(F + (2 + ch) * kFChunk) + off;
+                tc::mma_tf32(tmem, tc::smem_desc_sw128(xl), tc::smem_desc_sw128(fh), idesc, ks > 0);
+                tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fl), idesc, 1);
+                tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fh), idesc, 1);
+            }
+            tc::commit(&mma_done);
+        }
+        ok = tc::mbar_wait(&mma_done, k & 1, kTcWait) && ok;
+        tc::fence_after_sync();
+        const int m = warp * 32 + lane;
+        const int row = row0 + m;
+        float o[kM];
+        if (ok) {
+#pragma unroll
+            for (int c0 = 0; c0 < kM; c0 += 16)
+                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, o + c0);
+            tc::tmem_wait_ld();
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {               // delta form: + X (= hi + lo exactly)
+                    const int off = ch * kChunk + tc::sw128_off(m, j);
+                    const float4 h = *reinterpret_cast<const float4*>(Xh + off);
+                    const float4 l = *reinterpret_cast<const float4*>(Xl + off);
+                    float* oo = o + ch * 32 + j * 4;
+                    oo[0] += h.x + l.x; oo[1] += h.y + l.y; oo[2] += h.z + l.z; oo[3] += h.w + l.w;
+                }
+        }
+        if (!vt) {
+            if (ok && row < N) {
+                if (Sbuf && (row / kB == I || row / kB == J)) {
+                    const float* Sr = Sbuf + (size_t)b * kM * kM +
+                                      (size_t)(row / kB == I ? row % kB : kB + row % kB) * kM;
+#pragma unroll
+                    for (int c = 0; c < kM; ++c) o[c] = __ldg(Sr + c);
+                }
+#pragma unroll
+                for (int c = 0; c < kM; ++c) Tout[(size_t)row + (size_t)pair_global(c, I, J, kB) * N] = o[c];
+            }
+        } else if (ok) {
+            // stage in the slot's X area (read by the split only) and store with TMA
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float* oo = o + ch * 32 + j * 4;
+                    *reinterpret_cast<float4*>(sl + ch * kChunk + tc::sw128_off(m, j)) =
+                        make_float4(oo[0], oo[1], oo[2], oo[3]);
+                }
+            tc::fence_proxy_async();
+        }
+        tc::fence_before_sync();
+        __syncthreads();                             // TMEM, Xh/Xl and the staging tile are settled
+        const int itn = next_item(it + gridDim.x, total, items_T, n_slabs, fmax);
+        const int it2 = itn < total ? next_item(itn + gridDim.x, total, items_T, n_slabs, fmax) : total;
+        if (tid == 0) {
+            if (vt && ok) {
+                tc::tma_store_2d(&maps.v, I * kB, row0, sl);
+                tc::tma_store_2d(&maps.v, J * kB, row0, sl + kChunk);
+                tc::bulk_commit();
+                tc::bulk_wait_read();                // the slot is reloaded next
+            }
+            if (it2 < total) issue_item(maps, it2, items_T, n_slabs, round, nblocks, sl, &full[slot]);
+        }
+        it = itn;
+    }
+    if (!ok && tid == 0) atomicExch(err, 1ull);
+    if (tid == 0) tc::bulk_wait_all();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kM);
+}
+
+__global__ void k_gather_z32_rowmajor(const float* __restrict__ Vt, int ld, const int* __restrict__ perm,
+                                      int n, double* __restrict__ Z, int ldz) {
+    // Z[:, c] = V[:, perm[c]] with V row-major (V[r][p] = Vt[p + r ld]); one row of
+    // V per block iteration, so the reads of a row are served from one cache line set.
+    for (int r = blockIdx.x; r < n; r += gridDim.x) {
+        const float* row = Vt + (size_t)r * ld;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            int p = perm[c];
+            p = p < 0 ? 0 : (p >= n ? n - 1 : p);
+            Z[(size_t)r + (size_t)c * ldz] = (double)row[p];
+        }
+    }
+}
+
+}  // namespace
+
+size_t tc32_workspace_bytes(int N) {
+    const size_t K = (size_t)(N / kM);
+    return twosided_workspace_bytes<float>(N, kB) + sizeof(float) * K * kM * kM * 3 + 1024;
+}
+
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Row-major 2-D FP32 array (outer x inner, rows of `inner` floats) viewed in
+// boxes of box_outer rows x 32 floats, 128-byte swizzle.
+int encode_rows(CUtensorMap* m, const float* base, uint64_t inner, uint64_t outer, uint32_t box_outer) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) { set_error_msg("cuTensorMapEncodeTiled is not available"); return MPJ_CUDA_ERROR; }
+    cuuint64_t dims[2] = {inner, outer};
+    cuuint64_t strides[1] = {inner * sizeof(float)};
+    cuuint32_t box[2] = {32, box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) { set_error_msg("cuTensorMapEncodeTiled failed"); return MPJ_CUDA_ERROR; }
+    return MPJ_SUCCESS;
+}
+
+int sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            v = 148;
+        return v;
+    }();
+    return n;
+}
+
+}  // namespace
+
+int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double* Z, int ldz,
+                        cudaStream_t s) {
+    {
+        MPJ_PROF(PC_AUX, s);
+        k_gather_z32_rowmajor<<<n < 152 * 8 ? n : 152 * 8, 256, 0, s>>>(Vt, ld, perm, n, Z, ldz);
+    }
+    MPJ_LAUNCH_CHECK("k_gather_z32_rowmajor");
+    return MPJ_SUCCESS;
+}
+
+int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol_abs,
+                         double eps_skip, int max_sweeps, int max_inner, void* work, cudaStream_t s,
+                         SweepResult* res) {
+    if (N % kM != 0) { set_error_msg("tensor-core engine: N must be a multiple of 64"); return MPJ_BAD_ARG; }
+    const int K = N / kM;
+    Arena ar;
+    ar.base = static_cast<char*>(work);
+    ar.size = tc32_workspace_bytes(N);
+    float* Wbuf = ar.take<float>((size_t)K * kM * kM);
+    float* Sbuf = ar.take<float>((size_t)K * kM * kM);
+    float* Fimg = ar.take<float>((size_t)K * 2 * kM * kM);
+    float* fmax = ar.take<float>((size_t)K);
+    double* partial = ar.take<double>(1024);
+    double* offv = ar.take<double>(4);
+    unsigned long long* rot = ar.take<unsigned long long>(4);     // [0] rotations, [1] error flag
+    if (!Wbuf || !Sbuf || !Fimg || !fmax || !partial || !offv || !rot) {
+        set_error_msg("workspace too small");
+        return MPJ_BAD_ARG;
+    }
+    HostScratch hs;
+    MPJ_TRY(hs.init());
+    MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2_nb, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)InnerLayout<float, kM>::bytes));
+    MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
+    PassMaps maps1, maps2;
+    MPJ_TRY(encode_rows(&maps1.in_t, T, N, N, kSlab));
+    MPJ_TRY(encode_rows(&maps1.v, Vt, N, N, kSlab));
+    MPJ_TRY(encode_rows(&maps1.f, Fimg, kM, (uint64_t)K * 2 * kM, kM));
+    maps2 = maps1;
+    MPJ_TRY(encode_rows(&maps2.in_t, P, N, N, kSlab));
+    MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, 2 * sizeof(unsigned long long), s));
+    MPJ_TRY(offnorm2(T, false, N, n, partial, offv, s));
+    MPJ_CUDA_TRY(cudaMemcpyAsync(hs.d, offv, sizeof(double), cudaMemcpyDeviceToHost, s));
+    MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+    double off = sqrt(hs.d[0]);
+    res->off_initial = off;
+    res->sweeps = 0;
+    res->rotations = 0;
+    res->status = MPJ_NOT_CONVERGED;
+    const int rounds = 2 * K - 1;
+    const int n_slabs = (N + kSlab - 1) / kSlab;
+    const int items = n_slabs * K;
+    const int grid1 = items < sm_count() ? items : sm_count();
+    const int grid2 = 2 * items < sm_count() ? 2 * items : sm_count();
+    const float tau = (float)(tol_abs / (double)N);
+    const float gate = 1.0f / 4096.0f;                   // Newton-Schulz when some |F| >= 2^-12
+    while (res->sweeps < max_sweeps) {
+        if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
+        if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
+        MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        for (int r = 0; r < rounds; ++r) {
+            {
+                MPJ_PROF(PC_SOLVE2_F32, s);
+                k_solve2_nb<<<K, kSolveThreads, InnerLayout<float, kM>::bytes, s>>>(
+                    T, N, Wbuf, Sbuf, Fimg, fmax, r, (float)eps_skip, tau, gate, max_inner, rot);
+            }
+            MPJ_LAUNCH_CHECK("k_solve2_nb");
+            {
+                MPJ_PROF(PC_TC1_F32, s);
+                k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps1, P, N, n_slabs, items, items, nullptr,
+                                                               fmax, r, rot + 1);
+            }
+            MPJ_LAUNCH_CHECK("k_pass_tc pass 1");
+            {
+                MPJ_PROF(PC_TC2V_F32, s);
+                k_pass_tc<<<grid2, kTcThreads, kPassSmem, s>>>(maps2, T, N, n_slabs, items, 2 * items, Sbuf,
+                                                               fmax, r, rot + 1);
+            }
+            MPJ_LAUNCH_CHECK("k_pass_tc pass 2");
+        }
+        MPJ_TRY(offnorm2(T, false, N, n, partial, offv, s));
+        MPJ_CUDA_TRY(cudaMemcpyAsync(hs.d, offv, sizeof(double), cudaMemcpyDeviceToHost, s));
+        MPJ_CUDA_TRY(cudaMemcpyAsync(hs.u, rot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+        prof_flush();
+        if (hs.u[1]) { set_error_msg("tensor-core tile: MMA completion wait timed out"); return MPJ_CUDA_ERROR; }
+        off = sqrt(hs.d[0]);
+        res->sweeps += 1;
+        res->rotations += (double)hs.u[0];
+        if (trace_on())
+            fprintf(stderr, "[mpj] twosided<tc32> n=%d sweep %d: %llu rotations, off %.3e\n", n,
+                    res->sweeps, hs.u[0], off);
+        if (hs.u[0] == 0) { res->status = MPJ_SUCCESS; break; }
+    }
+    if (res->status == MPJ_NOT_CONVERGED && std::isfinite(off) && !(off > tol_abs))
+        res->status = MPJ_SUCCESS;
+    res->off_final = off;
+    return MPJ_SUCCESS;
+}
+
+}  // namespace mpj
