@@ -68,15 +68,16 @@ k_solve2_nb(float* __restrict__ T, int N, float* __restrict__ Fbuf, float* __res
 }
 
 // Per-CTA shared memory of the pass kernel (offsets in floats from a 1024-byte
-// aligned base).  Two load slots, each: the two 32-column chunks of the X tile
-// (128 rows x 128 bytes, 128-byte swizzle, as the TMA writes them) and the
-// TF32 hi/lo image of F_b^T for the two K halves (64 rows x 128 bytes each).
-// Then the hi and lo TF32 parts of X in the same layout (MMA operand A).
+// aligned base): the load slot -- the two 32-column chunks of the X tile (128
+// rows x 128 bytes, 128-byte swizzle, as the TMA writes them; split in place
+// into the TF32 hi part) and the TF32 hi/lo image of F_b^T for the two K halves
+// (64 rows x 128 bytes each) -- then the TF32 lo part of X.  96 KB: two CTAs
+// share an SM, so one's loads overlap the other's MMAs and stores.
 constexpr int kChunk = kSlab * 32;                   // floats of one X chunk (16 KB)
 constexpr int kFChunk = kM * 32;                     // floats of one F chunk (8 KB)
 constexpr int kSlotFloats = 2 * kChunk + 4 * kFChunk;
-constexpr int kXsplitOff = 2 * kSlotFloats;          // XhI, XhJ, XlI, XlJ
-constexpr size_t kPassSmem = sizeof(float) * (size_t)(kXsplitOff + 4 * kChunk) + 1024;
+constexpr int kXlOff = kSlotFloats;
+constexpr size_t kPassSmem = sizeof(float) * (size_t)(kXlOff + 2 * kChunk) + 1024;
 constexpr uint32_t kSlotBytes = sizeof(float) * kSlotFloats;   // TMA bytes per item
 
 struct PassMaps {
@@ -111,28 +112,27 @@ __device__ __forceinline__ void issue_item(const PassMaps& maps, int it, int ite
     tc::tma_load_2d(F + 3 * kFChunk, &maps.f, 32, b * 2 * kM + kM, full);  // lo, k >= 32
 }
 
-// Persistent pass kernel.  Items [0, items_T): Tout[rows, IJ_b] = X + X F_b with
-// X[m][k] = In[col(k) + (row0 + m) N] (In^T, K-major), written column-major;
-// with Sbuf the rows in IJ_b take the solver's rotated block instead.  Items
-// [items_T, total): the rows slab of the row-major V times W_b, stored back with
-// TMA.  Each CTA keeps two items in flight: the TMA loads of item k+2 are issued
-// as soon as item k has left its slot.
-__global__ void __launch_bounds__(kTcThreads, 1)
+// Persistent pass kernel (two CTAs per SM).  Items [0, items_T): Tout[rows, IJ_b]
+// = X + X F_b with X[m][k] = In[col(k) + (row0 + m) N] (In^T, K-major), written
+// column-major; with Sbuf the rows in IJ_b take the solver's rotated block
+// instead.  Items [items_T, total): the rows slab of the row-major V times W_b,
+// stored back with TMA.
+__global__ void __launch_bounds__(kTcThreads, 2)
 k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N, int n_slabs,
           int items_T, int total, const float* __restrict__ Sbuf, const float* __restrict__ fmax,
           int round, unsigned long long* __restrict__ err) {
     extern __shared__ unsigned char smraw[];
-    float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full[2];
+    float* sl = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    __shared__ __align__(8) uint64_t full;
     __shared__ __align__(8) uint64_t mma_done;
     __shared__ uint32_t tmem_slot;
-    float* Xh = sm + kXsplitOff;                     // XhI, XhJ
-    float* Xl = Xh + 2 * kChunk;                     // XlI, XlJ
+    float* Xh = sl;                                  // split in place
+    float* Xl = sl + kXlOff;
+    const float* F = sl + 2 * kChunk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nblocks = N / kB;
     if (tid == 0) {
-        tc::mbar_init(&full[0], 1);
-        tc::mbar_init(&full[1], 1);
+        tc::mbar_init(&full, 1);
         tc::mbar_init(&mma_done, 1);
         tc::fence_mbar_init();
     }
@@ -141,28 +141,22 @@ k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    int it0 = next_item(blockIdx.x, total, items_T, n_slabs, fmax);
-    int it1 = it0 < total ? next_item(it0 + gridDim.x, total, items_T, n_slabs, fmax) : total;
-    if (tid == 0) {
-        if (it0 < total) issue_item(maps, it0, items_T, n_slabs, round, nblocks, sm, &full[0]);
-        if (it1 < total) issue_item(maps, it1, items_T, n_slabs, round, nblocks, sm + kSlotFloats, &full[1]);
-    }
+    const int it0 = next_item(blockIdx.x, total, items_T, n_slabs, fmax);
+    if (tid == 0 && it0 < total) issue_item(maps, it0, items_T, n_slabs, round, nblocks, sl, &full);
     bool ok = true;
     int k = 0;
     for (int it = it0; it < total; ++k) {
-        const int slot = k & 1;
-        float* sl = sm + slot * kSlotFloats;
         const bool vt = it >= items_T;
         const int item = vt ? it - items_T : it;
         const int s = item % n_slabs, b = item / n_slabs;
         int I, J;
         round_pair(round, b, nblocks, I, J);
         const int row0 = s * kSlab;
-        ok = tc::mbar_wait(&full[slot], (k >> 1) & 1, kTcWait) && ok;       // waited even after an error
-        // split X (same swizzled offsets in the source and in Xh / Xl)
+        ok = tc::mbar_wait(&full, k & 1, kTcWait) && ok;         // waited even after an error
+        // split X in place: hi over the loaded tile, lo to Xl (same swizzled offsets)
 #pragma unroll 4
         for (int i = tid; i < 2 * kChunk / 4; i += kTcThreads) {
-            const float4 x = reinterpret_cast<const float4*>(sl)[i];
+            const float4 x = reinterpret_cast<const float4*>(Xh)[i];
             float4 h, l;
             tc::split_tf32(x.x, h.x, l.x);
             tc::split_tf32(x.y, h.y, l.y);
@@ -177,7 +171,6 @@ k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N
         tc::fence_after_sync();
         if (tid == 0 && ok) {
             constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, kSlab, kM);
-            const float* F = sl + 2 * kChunk;
 #pragma unroll
             for (int ks = 0; ks < kM / 8; ++ks) {          // K = 8 per MMA, 32 bytes along the row
                 const int ch = ks >> 2;
@@ -224,30 +217,32 @@ k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N
 #pragma unroll
                 for (int c = 0; c < kM; ++c) Tout[(size_t)row + (size_t)pair_global(c, I, J, kB) * N] = o[c];
             }
-        } else if (ok) {
-            // stage in the slot's X area (read by the split only) and store with TMA
+        } else {
+            __syncthreads();                         // every thread has read its X row
+            if (ok) {
+                // stage over the X tile and store with TMA
 #pragma unroll
-            for (int ch = 0; ch < 2; ++ch)
+                for (int ch = 0; ch < 2; ++ch)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float* oo = o + ch * 32 + j * 4;
-                    *reinterpret_cast<float4*>(sl + ch * kChunk + tc::sw128_off(m, j)) =
-                        make_float4(oo[0], oo[1], oo[2], oo[3]);
-                }
-            tc::fence_proxy_async();
+                    for (int j = 0; j < 8; ++j) {
+                        const float* oo = o + ch * 32 + j * 4;
+                        *reinterpret_cast<float4*>(Xh + ch * kChunk + tc::sw128_off(m, j)) =
+                            make_float4(oo[0], oo[1], oo[2], oo[3]);
+                    }
+                tc::fence_proxy_async();
+            }
         }
         tc::fence_before_sync();
-        __syncthreads();                             // TMEM, Xh/Xl and the staging tile are settled
+        __syncthreads();                             // TMEM, X and the staging tile are settled
         const int itn = next_item(it + gridDim.x, total, items_T, n_slabs, fmax);
-        const int it2 = itn < total ? next_item(itn + gridDim.x, total, items_T, n_slabs, fmax) : total;
         if (tid == 0) {
             if (vt && ok) {
-                tc::tma_store_2d(&maps.v, I * kB, row0, sl);
-                tc::tma_store_2d(&maps.v, J * kB, row0, sl + kChunk);
+                tc::tma_store_2d(&maps.v, I * kB, row0, Xh);
+                tc::tma_store_2d(&maps.v, J * kB, row0, Xh + kChunk);
                 tc::bulk_commit();
                 tc::bulk_wait_read();                // the slot is reloaded next
             }
-            if (it2 < total) issue_item(maps, it2, items_T, n_slabs, round, nblocks, sl, &full[slot]);
+            if (itn < total) issue_item(maps, itn, items_T, n_slabs, round, nblocks, sl, &full);
         }
         it = itn;
     }
@@ -378,8 +373,8 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     const int rounds = 2 * K - 1;
     const int n_slabs = (N + kSlab - 1) / kSlab;
     const int items = n_slabs * K;
-    const int grid1 = items < sm_count() ? items : sm_count();
-    const int grid2 = 2 * items < sm_count() ? 2 * items : sm_count();
+    const int grid1 = items < 2 * sm_count() ? items : 2 * sm_count();
+    const int grid2 = 2 * items < 2 * sm_count() ? 2 * items : 2 * sm_count();
     const float tau = (float)(tol_abs / (double)N);
     const float gate = 1.0f / 4096.0f;                   // Newton-Schulz when some |F| >= 2^-12
     while (res->sweeps < max_sweeps) {
