@@ -45,7 +45,8 @@ struct ApplySmem {
 template <class Real, int B, bool WriteBack = true>
 __device__ int pair_solve(Real* __restrict__ T, int N, int round, int pair, Real eps, Real tau,
                           Real gate, int max_inner, Real* __restrict__ Fout, float* fmax_out,
-                          unsigned char* smraw, Real* __restrict__ Sout = nullptr) {
+                          unsigned char* smraw, Real* __restrict__ Sout = nullptr,
+                          int cross_round = -1) {
     constexpr int M = 2 * B;
     constexpr int LD = M + 1;
     Real* S = reinterpret_cast<Real*>(smraw);
@@ -63,7 +64,7 @@ __device__ int pair_solve(Real* __restrict__ T, int N, int round, int pair, Real
         F[c * LD + r] = Real(0);
     }
     __syncthreads();
-    int applied = inner_jacobi<Real, M>(S, F, cs, ip, eps, tau, max_inner);
+    int applied = inner_jacobi<Real, M>(S, F, cs, ip, eps, tau, max_inner, cross_round);
     if (WriteBack) {
         for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
             int r = t % M, c = t / M;

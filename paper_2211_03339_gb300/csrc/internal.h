@@ -117,6 +117,8 @@ int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double*
                         cudaStream_t s);
 // The tensor-core engine is used for b = 32 unless MPJ_TC=0 (comparison switch).
 bool tc_enabled();
+// Inner schedule of the block solves (1: cross pairs, see inner_jacobi).
+int cross_schedule(bool fp64);
 
 // One-sided block Jacobi (Alg. 5.1 / steps 4-10 of Alg. 5.2) on C (m x N, ld = ldc)
 // and V (N x N, ld = N).

@@ -59,8 +59,14 @@ struct InnerLayout {
 // test).  Stops after an inner sweep with no rotation or after max_inner
 // sweeps.  Returns the number of rotations applied (all threads).
 // Must be called by all threads of the block (any multiple of 32, at least 256).
+// With cross_round >= 0 an inner sweep is the M/2 steps that rotate every pair
+// (i, j) with i in the first block and j in the second once, followed by one
+// step over pairs inside each block (round cross_round mod (M/2 - 1) of the
+// tournament over that block), so that over the rounds of an outer sweep every
+// intra-block pair is still visited.
 template <class Real, int M>
-__device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real tau, int max_inner) {
+__device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real tau, int max_inner,
+                            int cross_round = -1) {
     constexpr int LD = M + 1;
     constexpr int P = M / 2;
     static_assert(P <= 32, "pair count must fit one warp");
@@ -74,11 +80,23 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
     int total = 0;
     for (int sweep = 0; sweep < max_inner; ++sweep) {
         int applied = 0;
-        for (int r = 0; r < M - 1; ++r) {
+        const int nsteps = cross_round >= 0 ? P + 1 : M - 1;
+        for (int r = 0; r < nsteps; ++r) {
             if (tid < 32) {
                 int mine = 0;
                 if (tid < P) {
-                    int p = rr_index(r, tid, M), q = rr_index(r, M - 1 - tid, M);
+                    int p, q;
+                    if (cross_round < 0) {
+                        p = rr_index(r, tid, M);
+                        q = rr_index(r, M - 1 - tid, M);
+                    } else if (r < P) {
+                        p = tid;
+                        q = P + (tid + r) % P;
+                    } else {
+                        const int qr = cross_round % (P - 1), h = tid / (P / 2), i = tid % (P / 2);
+                        p = h * P + rr_index(qr, i, P);
+                        q = h * P + rr_index(qr, P - 1 - i, P);
+                    }
                     if (p > q) { int t = p; p = q; q = t; }
                     Real apq = S[q * LD + p], app = S[p * LD + p], aqq = S[q * LD + q];
                     Real c = Real(1), s = Real(0), t = Real(0);

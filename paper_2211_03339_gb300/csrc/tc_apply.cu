@@ -26,6 +26,7 @@
 // the diagonal blocks too).
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 
 #include <cuda.h>
 
@@ -47,12 +48,12 @@ constexpr int kM = 2 * kB;
 __global__ void __launch_bounds__(kSolveThreads)
 k_solve2_nb(float* __restrict__ T, int N, float* __restrict__ Fbuf, float* __restrict__ Sbuf,
             float* __restrict__ Fimg, float* __restrict__ fmax, int round, float eps, float tau,
-            float gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
+            float gate, int max_inner, int cross, unsigned long long* __restrict__ rot_counter) {
     extern __shared__ __align__(16) unsigned char smraw[];
     int applied = pair_solve<float, kB, false>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
                                                Fbuf + (size_t)blockIdx.x * kM * kM,
                                                fmax + blockIdx.x, smraw,
-                                               Sbuf + (size_t)blockIdx.x * kM * kM);
+                                               Sbuf + (size_t)blockIdx.x * kM * kM, cross ? round : -1);
     if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
     // TF32 hi / lo image of F_b^T (row n, column k holds F_b[k][n]) for the pass
     // kernel's B operand; the block's F is still in shared memory (after S).
@@ -377,6 +378,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     const int grid2 = 2 * items < 2 * sm_count() ? 2 * items : 2 * sm_count();
     const float tau = (float)(tol_abs / (double)N);
     const float gate = 1.0f / 4096.0f;                   // Newton-Schulz when some |F| >= 2^-12
+    const int cross = N >= kB * kB ? cross_schedule(false) : 0;     // see cross_schedule
     while (res->sweeps < max_sweeps) {
         if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
@@ -385,7 +387,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
             {
                 MPJ_PROF(PC_SOLVE2_F32, s);
                 k_solve2_nb<<<K, kSolveThreads, InnerLayout<float, kM>::bytes, s>>>(
-                    T, N, Wbuf, Sbuf, Fimg, fmax, r, (float)eps_skip, tau, gate, max_inner, rot);
+                    T, N, Wbuf, Sbuf, Fimg, fmax, r, (float)eps_skip, tau, gate, max_inner, cross, rot);
             }
             MPJ_LAUNCH_CHECK("k_solve2_nb");
             {

@@ -26,11 +26,12 @@ namespace mpj {
 template <class Real, int B>
 __global__ void __launch_bounds__(kSolveThreads)
 k_solve2(Real* __restrict__ T, int N, Real* __restrict__ Fbuf, float* __restrict__ fmax, int round,
-         Real eps, Real tau, Real gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
+         Real eps, Real tau, Real gate, int max_inner, int cross, unsigned long long* __restrict__ rot_counter) {
     constexpr int M = 2 * B;
     extern __shared__ __align__(16) unsigned char smraw[];
     int applied = pair_solve<Real, B>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
-                                      Fbuf + (size_t)blockIdx.x * M * M, fmax + blockIdx.x, smraw);
+                                      Fbuf + (size_t)blockIdx.x * M * M, fmax + blockIdx.x, smraw, nullptr,
+                                      cross ? round : -1);
     if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
 }
 
@@ -51,6 +52,22 @@ k_apply2V(Real* __restrict__ V, int N, const Real* __restrict__ Fbuf, const floa
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = N / (2 * B);
     apply_slab<Real, B>(V, N, Fbuf, fmax, round, blockIdx.x / K, blockIdx.x % K, df_gate, smraw);
+}
+
+// Inner-sweep schedule of the block solves: the cross-pair schedule (inner_jacobi
+// with cross_round) for the FP32 sweeps of step 1, where it halves the steps of a
+// block solve at the same outer sweep count; the full tournament for the FP64
+// sweeps, where the cross schedule leaves larger block rotations on clustered
+// spectra (fewer tiles qualify for the double-float products).  MPJ_CROSS=0 / 1
+// forces one schedule everywhere, for comparisons.  The callers use it only
+// when an outer sweep has at least b - 1 rounds (N >= b^2), so that the intra
+// steps of the rounds of one sweep cover every pair inside a block.
+int cross_schedule(bool fp64) {
+    static const int forced = [] {
+        const char* e = std::getenv("MPJ_CROSS");
+        return e && (*e == '0' || *e == '1') ? *e - '0' : -1;
+    }();
+    return forced >= 0 ? forced : (fp64 ? 0 : 1);
 }
 
 // MPJ_DF_GATE overrides the double-float gate (a negative value disables the
@@ -93,7 +110,7 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
     const bool dbl = sizeof(Real) == 8;
     { MPJ_PROF(dbl ? PC_SOLVE2_F64 : PC_SOLVE2_F32, s);
       k_solve2<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(T, N, Wbuf, fmax, r, eps, tau,
-                                                                         gate, max_inner, rot); }
+                                                                         gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot); }
     MPJ_LAUNCH_CHECK("k_solve2");
     int n_ttiles = K * (K - 1) / 2;
     if (n_ttiles > 0) {
