@@ -88,11 +88,37 @@ int read_scalar(const double* dval, double* out, cudaStream_t s) {
     return MPJ_SUCCESS;
 }
 
+// Status flag of a driver: bit 1 rank deficiency (a zero column), bit 2 a
+// tensor-core wait that timed out (reported as a CUDA error).
 int read_flag(const int* dflag, int* out, cudaStream_t s) {
     int h = 0;
     MPJ_CUDA_TRY(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
     MPJ_CUDA_TRY(cudaStreamSynchronize(s));
-    *out = h;
+    if (h & 2) { set_error_msg("tensor-core product: MMA or TMA wait timed out"); return MPJ_CUDA_ERROR; }
+    *out = h & 1;
+    return MPJ_SUCCESS;
+}
+
+// T = Q^T (A Q) with the upper triangle mirrored (T exactly symmetric), A
+// symmetric; W (n x n) is scratch.  With the two operand buffers (oz_operand_bytes
+// (n, n) each) both products run on the tensor cores by exact splitting
+// (ozaki.cu); the slices of Q serve as the columns of Q in A Q and as the rows
+// of Q^T in Q^T W.
+int congruence_fp64(const double* A, int lda, const double* Q, int ldq, int n, double* W, double* T,
+                    int ldt, void* oz1, void* oz2, int* d_flag, cudaStream_t s) {
+    if (oz1 && oz2 && oz_enabled() && oz_supported(n, n, n)) {
+        OzOperand oa, oq;
+        MPJ_TRY(oz_operand(oz1, n, n, &oa));
+        MPJ_TRY(oz_operand(oz2, n, n, &oq));
+        MPJ_TRY(oz_slice(A, lda, 1, n, n, &oa, s));        // rows of A (= its columns)
+        MPJ_TRY(oz_slice(Q, ldq, 1, n, n, &oq, s));        // columns of Q
+        MPJ_TRY(oz_gemm(oa, oq, 1.0, 0.0, W, n, false, d_flag, s));
+        MPJ_TRY(oz_slice(W, n, 1, n, n, &oa, s));          // columns of W
+        MPJ_TRY(oz_gemm(oq, oa, 1.0, 0.0, T, ldt, true, d_flag, s));
+        return MPJ_SUCCESS;
+    }
+    MPJ_TRY(dgemm(false, false, n, n, n, 1.0, A, lda, Q, ldq, 0.0, W, n, false, s));
+    MPJ_TRY(dgemm(true, false, n, n, n, 1.0, Q, ldq, W, n, 0.0, T, ldt, true, s));
     return MPJ_SUCCESS;
 }
 
@@ -112,6 +138,7 @@ struct EvdBufs {
     float *T32, *V32;
     void* eng;
     void* mgsw;
+    void *oz1, *oz2;             // tensor-core operand slices (mp only)
     Scal sc;
 };
 
@@ -130,8 +157,11 @@ int evd_layout(Arena& a, int n, int N, int B, bool mp, EvdBufs& b) {
     b.V32 = mp ? a.take<float>(NN) : nullptr;
     b.eng = a.take<char>(evd_engine_bytes(N, B));
     b.mgsw = mp ? a.take<char>(mgs_workspace_bytes(n, n)) : nullptr;
+    b.oz1 = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
+    b.oz2 = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
     MPJ_TRY(take_scal(a, n, b.sc));
-    if (a.base && (!b.T64 || !b.V64 || !b.eng || (mp && (!b.Q || !b.Wt || !b.T32 || !b.V32 || !b.mgsw))))
+    if (a.base && (!b.T64 || !b.V64 || !b.eng ||
+                   (mp && (!b.Q || !b.Wt || !b.T32 || !b.V32 || !b.mgsw || !b.oz1 || !b.oz2))))
         return MPJ_BAD_ARG;
     return MPJ_SUCCESS;
 }
@@ -210,9 +240,8 @@ int syevj_impl(bool mp, const double* A, int n, int lda, double* Lambda, double*
         MPJ_CUDA_TRY(cudaMemsetAsync(b.sc.flag, 0, sizeof(int), s));
         MPJ_TRY(mgs_inplace(b.Q, n, n, n, b.mgsw, b.sc.flag, s));                          // step 2
         tm.mark(2);
-        MPJ_TRY(dgemm(false, false, n, n, n, 1.0, A, lda, b.Q, n, 0.0, b.Wt, n, false, s)); // step 3
-        MPJ_CUDA_TRY(cudaMemsetAsync(b.T64, 0, sizeof(double) * (size_t)N * N, s));
-        MPJ_TRY(dgemm(true, false, n, n, n, 1.0, b.Q, n, b.Wt, n, 0.0, b.T64, N, true, s));
+        MPJ_CUDA_TRY(cudaMemsetAsync(b.T64, 0, sizeof(double) * (size_t)N * N, s));        // step 3
+        MPJ_TRY(congruence_fp64(A, lda, b.Q, n, n, b.Wt, b.T64, N, b.oz1, b.oz2, b.sc.flag, s));
         MPJ_TRY(copy_pad_f64(b.Q, n, n, n, b.V64, N, N, N, true, s));                      // P = Q
         tm.mark(3);
         int fl = 0;
@@ -462,7 +491,9 @@ int mpj_mgs(const double* Z, int m, int n, int ldz, double* Q, int ldq, void* wo
     return fl ? MPJ_RANK_DEFICIENT : MPJ_SUCCESS;
 }
 
-size_t mpj_congruence_workspace_bytes(int n) { return n < 1 ? 0 : sizeof(double) * (size_t)n * n + 512; }
+size_t mpj_congruence_workspace_bytes(int n) {
+    return n < 1 ? 0 : sizeof(double) * (size_t)n * n + 2 * oz_operand_bytes(n, n) + 4096;
+}
 
 int mpj_congruence(const double* A, int lda, const double* Q, int ldq, int n, double* T, int ldt,
                    void* work, size_t work_bytes, void* stream) {
@@ -471,10 +502,18 @@ int mpj_congruence(const double* A, int lda, const double* Q, int ldq, int n, do
     Workspace ws;
     size_t need = mpj_congruence_workspace_bytes(n);
     MPJ_TRY(ws.acquire(work, work_bytes, need, s));
-    double* W = static_cast<double*>(ws.ptr);
-    MPJ_TRY(dgemm(false, false, n, n, n, 1.0, A, lda, Q, ldq, 0.0, W, n, false, s));
-    MPJ_TRY(dgemm(true, false, n, n, n, 1.0, Q, ldq, W, n, 0.0, T, ldt, true, s));
-    MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+    Arena a;
+    a.base = static_cast<char*>(ws.ptr);
+    a.size = work ? work_bytes : need;
+    double* W = a.take<double>((size_t)n * n);
+    void* oz1 = a.take<char>(oz_operand_bytes(n, n));
+    void* oz2 = a.take<char>(oz_operand_bytes(n, n));
+    int* flag = a.take<int>(4);
+    if (!W || !oz1 || !oz2 || !flag) { set_error_msg("workspace layout"); return MPJ_BAD_ARG; }
+    MPJ_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
+    MPJ_TRY(congruence_fp64(A, lda, Q, ldq, n, W, T, ldt, oz1, oz2, flag, s));
+    int fl = 0;
+    MPJ_TRY(read_flag(flag, &fl, s));
     return MPJ_SUCCESS;
 }
 

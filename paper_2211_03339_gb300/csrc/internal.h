@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <cstddef>
 #include <cstdint>
 
@@ -70,7 +71,7 @@ enum ProfClass {
     PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
     PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2V_F32,
-    kProfClasses
+    PC_OZ_SLICE, PC_OZ_GEMM, kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -139,6 +140,30 @@ int dgemm(bool transA, bool transB, int M, int N, int K, double alpha, const dou
 int dgemm_batched(bool transA, bool transB, int M, int N, int K, double alpha, const double* A,
                   int lda, long long sA, const double* B, int ldb, long long sB, double beta,
                   double* C, int ldc, long long sC, int batch, bool upper_mirror, cudaStream_t s);
+
+// FP64 products on the bf16 tensor cores by exact splitting (ozaki.cu).  An
+// operand holds the 8 bf16 slice planes of `rows` rows of length K (row i of
+// op(A), or column j of op(B)) and the binary exponent of each row.
+struct OzOperand {
+    __nv_bfloat16* planes;
+    int* ex;
+    int rows, K;
+};
+size_t oz_operand_bytes(int rows, int K);
+int oz_operand(void* base, int rows, int K, OzOperand* op);
+bool oz_supported(int M, int N, int K);
+// MPJ_OZAKI=0 keeps every FP64 product on the FP64 pipe (comparison switch).
+bool oz_enabled();
+// Slice rows: row r is X[r * row_stride + k * k_stride], k < K (k_stride 1 or the
+// rows of a column-major matrix, row_stride 1).
+int oz_slice(const double* X, long long row_stride, long long k_stride, int rows, int K, OzOperand* op,
+             cudaStream_t s);
+// C (ld ldc) = alpha * A B^T-of-the-operands + beta C: C_ij = alpha sum_k opA(i,k) opB(k,j)
+// + beta C_ij with A holding the rows of op(A) and B the columns of op(B).  With
+// upper_mirror (square C) the upper triangle is mirrored onto the lower.  A
+// timed-out tensor-core wait sets bit 2 of *d_flag.
+int oz_gemm(const OzOperand& A, const OzOperand& B, double alpha, double beta, double* C, int ldc,
+            bool upper_mirror, int* d_flag, cudaStream_t s);
 
 // Blocked MGS (Lemma 2.1) in place on Q (m x n, ld = ldq).  Needs n x 32 doubles
 // of workspace for the panel projections.

@@ -371,7 +371,7 @@ __global__ void k_svd_post(const double* __restrict__ C, int ldc, const double* 
     double inv = sg > 0.0 ? 1.0 / sg : 0.0;
     if (threadIdx.x == 0) {
         Sigma[j] = sg;
-        if (!(sg > 0.0)) atomicExch(flag, 1);
+        if (!(sg > 0.0)) atomicOr(flag, 1);
     }
     for (int r = threadIdx.x; r < m; r += blockDim.x) U[(size_t)r + (size_t)j * ldu] = C[(size_t)r + (size_t)p * ldc] * inv;
     for (int r = threadIdx.x; r < n; r += blockDim.x) V[(size_t)r + (size_t)j * ldv] = Vw[(size_t)r + (size_t)p * ldvw];

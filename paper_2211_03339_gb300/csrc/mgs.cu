@@ -63,7 +63,7 @@ k_mgs_panel(double* __restrict__ Q, int m, int ldq, int j0, int pb, int* __restr
         __syncthreads();
         const double rjj = sqrt(red[jj]);
         if (rjj == 0.0 || !(rjj == rjj)) {
-            if (threadIdx.x == 0 && rank == 0) atomicExch(flag, 1);
+            if (threadIdx.x == 0 && rank == 0) atomicOr(flag, 1);
         }
         const double inv = (rjj > 0.0) ? 1.0 / rjj : 0.0;
         // q_j = w_j / r_jj ; w_k -= (g_k / r_jj) q_j for k > jj

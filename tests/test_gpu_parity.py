@@ -287,3 +287,21 @@ def test_gesvj_8192x1024_properties(mpj):
     assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
     assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
     assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
+
+
+@pytest.mark.parametrize("n", [129, 1000, 2500])
+def test_congruence_tensor_core_accuracy(mpj, n):
+    """Step 3 on the tensor cores (exact bf16 splitting) against an FP64 product
+    formed in numpy: the error must stay within the FP64 bound of the plain product
+    and near FP64 rounding in the Frobenius norm (a plausible slicing error -- a
+    dropped slice, a wrong exponent -- is orders of magnitude above both)."""
+    A, _ = synth.sym_matrix(n, "uniform", seed=700 + n)
+    Q = synth.haar(synth.rng_for(800 + n), n)
+    Tg = host(mpj.congruence(dev(A), dev(Q)))
+    Tn = Q.T @ (A @ Q)
+    Tn = np.triu(Tn) + np.triu(Tn, 1).T
+    assert np.array_equal(Tg, Tg.T)
+    gn = n * U / (1 - n * U)
+    bound = gn * (2 + gn) * (np.abs(Q).T @ np.abs(A) @ np.abs(Q))
+    assert (np.abs(Tg - Tn) <= 2 * bound).all()
+    assert np.linalg.norm(Tg - Tn) <= 4 * np.sqrt(n) * U * np.linalg.norm(A)
