@@ -110,6 +110,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_hbm():
+    """HBM copy bandwidth measured on the GB300s (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured STREAM-style copy (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def measured_bf16():
+    """Dense bf16 tensor throughput measured on the GB300s (burst)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured cuBLAS bf16 GEMM, burst (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16"
+
+
 def source_sha():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_03339_gb300", "csrc")
@@ -422,33 +440,52 @@ def run_ours(args):
     if rank != 0:
         return 0
 
-    # roofline of the dominant kernel class (largest summed event time among the
-    # classes with an algorithmic count; SURVEY-style per-solve counts:
-    # Alg. 3.2 sweep = 6 n^3 (3 n^3 for T, 3 n^3 for V), MGS 2 n^3 (projections n^3,
-    # trailing update n^3), congruence 3 n^3)
+    # roofline of every kernel class with an algorithmic count, and of the dominant
+    # one (largest summed event time).  Per-solve counts: Alg. 3.2 sweep = 6 n^3
+    # (3 n^3 for T, 3 n^3 for V), MGS 2 n^3 (projections n^3, trailing update n^3
+    # on the FP64 pipe), congruence 4 n^3 FP64 flops as two full products on the
+    # bf16 tensor cores, each FP64 flop being 36 bf16 slice-product flops; slicing
+    # reads 8 and writes 16 bytes per element of A, Q and W.  The
+    # tensor-core passes of step 1 are bound by HBM: each round reads and writes T
+    # (pass 1 writes P, pass 2 reads it) and V once: 8 N^2 bytes for pass 1 and
+    # 16 N^2 for pass 2 + V, N the padded order, N/32 - 1 rounds per sweep.
     sw64, sw32 = stats["sweeps"], stats["sweeps_stage1"]
-    alg = {"dgemm_f64": 4.0 * n ** 3, "mgs_proj": 1.0 * n ** 3,
+    Np = -(-n // 64) * 64
+    rounds = Np // 32 - 1
+    alg = {"dgemm_f64": 1.0 * n ** 3, "mgs_proj": 1.0 * n ** 3,
+           "oz_gemm": 36 * 4.0 * n ** 3, "oz_slice": 72.0 * n * n,
            "apply2_f64": 3.0 * n ** 3 * sw64, "apply2v_f64": 3.0 * n ** 3 * sw64,
-           "apply2_f32": 3.0 * n ** 3 * sw32, "apply2v_f32": 3.0 * n ** 3 * sw32}
+           "apply2_f32": 3.0 * n ** 3 * sw32, "apply2v_f32": 3.0 * n ** 3 * sw32,
+           "tc1_f32": 8.0 * Np * Np * rounds * sw32, "tc2v_f32": 16.0 * Np * Np * rounds * sw32}
     fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
     df_peak = 152 * 128 / 11 * 2 * 2.070e9 / 1e12     # 11 FP32 instructions per double-float MAC
-    peaks = {"dgemm_f64": (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
-             "mgs_proj": (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"),
-             "apply2_f64": (df_peak, "double-float on FP32: 152 x 128 lanes / 11 instr per MAC x 2 x 2.07 GHz"),
-             "apply2v_f64": (df_peak, "double-float on FP32: 152 x 128 lanes / 11 instr per MAC x 2 x 2.07 GHz"),
-             "apply2_f32": (fp32_peak, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz"),
-             "apply2v_f32": (fp32_peak, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz")}
-    cands = {k: v for k, v in prof.items() if k in alg and v[0] > 0}
-    dname, (dlaunch, dms) = max(cands.items(), key=lambda kv: kv[1][1])
-    per_launch_alg = alg[dname] * args.steps / dlaunch
-    avg_s = dms / dlaunch / 1e3
-    achieved = per_launch_alg / avg_s / 1e12
-    pk, note = peaks[dname]
-    roof = {"kernel": dname, "bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-            "frac": achieved / pk, "traffic": profiled_traffic(n, dname), "launches": dlaunch,
-            "avg_launch_ms": dms / dlaunch, "alg_flops_per_launch": per_launch_alg,
-            "peak_note": note + " (nominal; see DESIGN.md for the measured probe rates)",
-            "share_of_step": dms / total_ms}
+    hbm_peak, hbm_note = measured_hbm()
+    fp64 = (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (nominal; DESIGN.md has the probe rates)", "alu", "TFLOP/s")
+    dfp = (df_peak, "double-float on FP32: 152 x 128 lanes / 11 instr per MAC x 2 x 2.07 GHz", "alu", "TFLOP/s")
+    f32p = (fp32_peak, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz", "alu", "TFLOP/s")
+    hbm = (hbm_peak, hbm_note, "hbm", "GB/s")
+    bf16_peak, bf16_note = measured_bf16()
+    tensor = (bf16_peak, bf16_note + "; the FP64-equivalent rate is achieved / 36 (36 slice products)",
+              "tensor", "TFLOP/s")
+    peaks = {"dgemm_f64": fp64, "mgs_proj": fp64, "apply2_f64": dfp, "apply2v_f64": dfp,
+             "apply2_f32": f32p, "apply2v_f32": f32p, "tc1_f32": hbm, "tc2v_f32": hbm,
+             "oz_gemm": tensor, "oz_slice": hbm}
+    rooflines = {}
+    for name, (nl, ms) in prof.items():
+        if name not in alg or nl == 0:
+            continue
+        per_launch = alg[name] * args.steps / nl
+        avg_s = ms / nl / 1e3
+        pk, note, bound, unit = peaks[name]
+        scale = 1e9 if unit == "GB/s" else 1e12
+        achieved = per_launch / avg_s / scale
+        rooflines[name] = {"kernel": name, "bound": bound, "achieved": achieved, "peak": pk, "unit": unit,
+                           "frac": achieved / pk, "traffic": profiled_traffic(n, name), "launches": nl,
+                           "avg_launch_ms": ms / nl,
+                           ("alg_bytes_per_launch" if unit == "GB/s" else "alg_flops_per_launch"): per_launch,
+                           "peak_note": note, "share_of_step": ms / total_ms}
+    dname = max(rooflines, key=lambda k: rooflines[k]["share_of_step"])
+    roof = rooflines[dname]
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -468,6 +505,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": 8 * n * n, "d2h_bytes_per_step": 8 * n * n + 8 * n},
         "gpu_launches": launches,
         "roofline": roof,
+        "rooflines": {k: {kk: v[kk] for kk in ("bound", "achieved", "peak", "unit", "frac", "share_of_step")}
+                      for k, v in rooflines.items()},
         "cpu_baseline": cpu,
         "stages_ms": stats["ms_stage"], "sweeps": stats["sweeps"],
         "sweeps_stage1": stats["sweeps_stage1"], "off_T0": stats["off_T0"],
