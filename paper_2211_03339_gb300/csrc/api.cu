@@ -138,7 +138,7 @@ struct EvdBufs {
     float *T32, *V32;
     void* eng;
     void* mgsw;
-    void *oz1, *oz2;             // tensor-core operand slices (mp only)
+    void *oz1, *oz2, *ozs;       // tensor-core operand slices (mp only)
     Scal sc;
 };
 
@@ -159,9 +159,10 @@ int evd_layout(Arena& a, int n, int N, int B, bool mp, EvdBufs& b) {
     b.mgsw = mp ? a.take<char>(mgs_workspace_bytes(n, n)) : nullptr;
     b.oz1 = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
     b.oz2 = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
+    b.ozs = mp ? a.take<char>(mgs_panel_oz_bytes(n, n)) : nullptr;
     MPJ_TRY(take_scal(a, n, b.sc));
     if (a.base && (!b.T64 || !b.V64 || !b.eng ||
-                   (mp && (!b.Q || !b.Wt || !b.T32 || !b.V32 || !b.mgsw || !b.oz1 || !b.oz2))))
+                   (mp && (!b.Q || !b.Wt || !b.T32 || !b.V32 || !b.mgsw || !b.oz1 || !b.oz2 || !b.ozs))))
         return MPJ_BAD_ARG;
     return MPJ_SUCCESS;
 }
@@ -238,7 +239,11 @@ int syevj_impl(bool mp, const double* A, int n, int lda, double* Lambda, double*
         MPJ_TRY(stage1_evd(A, lda, n, N, B, normA, op, b, &r1, s));                       // step 1
         tm.mark(1);
         MPJ_CUDA_TRY(cudaMemsetAsync(b.sc.flag, 0, sizeof(int), s));
-        MPJ_TRY(mgs_inplace(b.Q, n, n, n, b.mgsw, b.sc.flag, s));                          // step 2
+        if (n >= 1024 && oz_enabled() && oz_supported(n, n, n)) {                           // step 2
+            MPJ_TRY(mgs_blocked_oz(b.Q, n, n, n, b.mgsw, b.sc.flag, b.oz1, b.ozs, b.Wt, s));
+        } else {
+            MPJ_TRY(mgs_inplace(b.Q, n, n, n, b.mgsw, b.sc.flag, s));
+        }
         tm.mark(2);
         MPJ_CUDA_TRY(cudaMemsetAsync(b.T64, 0, sizeof(double) * (size_t)N * N, s));        // step 3
         MPJ_TRY(congruence_fp64(A, lda, b.Q, n, n, b.Wt, b.T64, N, b.oz1, b.oz2, b.sc.flag, s));
@@ -468,7 +473,15 @@ int mpj_stage1_syevj32(const double* A, int n, int lda, double* Z, int ldz, doub
     return r1.status;
 }
 
-size_t mpj_mgs_workspace_bytes(int m, int n) { return mgs_workspace_bytes(m, n) + 1024; }
+// Large problems take the block MGS whose panel projections run on the tensor cores.
+static bool mgs_use_oz(int m, int n) { return n >= 1024 && oz_enabled() && oz_supported(n, n, m); }
+
+size_t mpj_mgs_workspace_bytes(int m, int n) {
+    size_t b = mgs_workspace_bytes(m, n) + 1024;
+    if (m >= 1 && n >= 1 && mgs_use_oz(m, n))
+        b += oz_operand_bytes(n, m) + mgs_panel_oz_bytes(m, n) + sizeof(double) * 256 * (size_t)n + 1024;
+    return b;
+}
 
 int mpj_mgs(const double* Z, int m, int n, int ldz, double* Q, int ldq, void* work,
             size_t work_bytes, void* stream) {
@@ -485,7 +498,15 @@ int mpj_mgs(const double* Z, int m, int n, int ldz, double* Q, int ldq, void* wo
     if (!flag || !mw) { set_error_msg("workspace layout"); return MPJ_BAD_ARG; }
     MPJ_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), s));
     MPJ_TRY(copy_f64(Z, ldz, m, n, Q, ldq, s));
-    MPJ_TRY(mgs_inplace(Q, m, n, ldq, mw, flag, s));
+    if (mgs_use_oz(m, n)) {
+        void* ozw = a.take<char>(oz_operand_bytes(n, m));
+        void* ozs = a.take<char>(mgs_panel_oz_bytes(m, n));
+        double* rb = a.take<double>(256 * (size_t)n);
+        if (!ozw || !ozs || !rb) { set_error_msg("workspace layout"); return MPJ_BAD_ARG; }
+        MPJ_TRY(mgs_blocked_oz(Q, m, n, ldq, mw, flag, ozw, ozs, rb, s));
+    } else {
+        MPJ_TRY(mgs_inplace(Q, m, n, ldq, mw, flag, s));
+    }
     int fl = 0;
     MPJ_TRY(read_flag(flag, &fl, s));
     return fl ? MPJ_RANK_DEFICIENT : MPJ_SUCCESS;

@@ -169,6 +169,12 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, double alpha, double beta, d
 // of workspace for the panel projections.
 size_t mgs_workspace_bytes(int m, int n);
 int mgs_inplace(double* Q, int m, int n, int ldq, void* work, int* d_flag, cudaStream_t s);
+// The same with 256-column panels whose mutual projections run on the tensor
+// cores (mgs.cu); ozW: oz_operand_bytes(n, m), ozS: mgs_panel_oz_bytes(m, n),
+// Rbuf: 256 x n doubles.
+size_t mgs_panel_oz_bytes(int m, int n);
+int mgs_blocked_oz(double* Q, int m, int n, int ldq, void* work, int* d_flag, void* ozW, void* ozS,
+                   double* Rbuf, cudaStream_t s);
 
 // ---------------------------------------------------------------- helpers (kernels.cu)
 int copy_pad_f64(const double* A, int lda, int rows, int cols, double* T, int ldt, int Rpad,

@@ -181,6 +181,49 @@ int mgs_inplace(double* Q, int m, int n, int ldq, void* work, int* d_flag, cudaS
     return MPJ_SUCCESS;
 }
 
+// Block MGS with 256-column panels: each panel is orthogonalised by the 32-column
+// blocked MGS above, then the trailing columns W lose their projection on it,
+// W <- W - Q_p (Q_p^T W) -- the projection (K = m) and the update (K = 256) on
+// the tensor cores by exact splitting.  Panels are processed in order, each
+// against the already updated W (modified Gram-Schmidt at the panel level).
+// ozW: oz_operand_bytes(n, m) (columns of W); ozS: mgs_panel_oz_bytes(m, n);
+// Rbuf: 256 x n doubles.
+size_t mgs_panel_oz_bytes(int m, int n) {
+    return oz_operand_bytes(256, m) + oz_operand_bytes(m, 256) + oz_operand_bytes(n, 256) + 1024;
+}
+
+int mgs_blocked_oz(double* Q, int m, int n, int ldq, void* work, int* d_flag, void* ozW, void* ozS,
+                   double* Rbuf, cudaStream_t s) {
+    constexpr int BP = 256;
+    char* base = static_cast<char*>(ozS);
+    OzOperand opT, opR, oR, oW;
+    const size_t a1 = (oz_operand_bytes(256, m) + 255) & ~size_t(255);
+    const size_t a2 = (oz_operand_bytes(m, 256) + 255) & ~size_t(255);
+    MPJ_TRY(oz_operand(base, 256, m, &opT));
+    MPJ_TRY(oz_operand(base + a1, m, 256, &opR));
+    MPJ_TRY(oz_operand(base + a1 + a2, n, 256, &oR));
+    MPJ_TRY(oz_operand(ozW, n, m, &oW));
+    for (int j0 = 0; j0 < n; j0 += BP) {
+        const int nb = n - j0 < BP ? n - j0 : BP;
+        double* Qp = Q + (size_t)j0 * ldq;
+        MPJ_TRY(mgs_inplace(Qp, m, nb, ldq, work, d_flag, s));
+        const int rest = n - j0 - nb;
+        if (rest <= 0) break;
+        double* W = Q + (size_t)(j0 + nb) * ldq;
+        opT.rows = nb; opT.K = m;
+        oW.rows = rest; oW.K = m;
+        MPJ_TRY(oz_slice(Qp, ldq, 1, nb, m, &opT, s));          // rows of Q_p^T (columns of Q_p)
+        MPJ_TRY(oz_slice(W, ldq, 1, rest, m, &oW, s));          // columns of W
+        MPJ_TRY(oz_gemm(opT, oW, 1.0, 0.0, Rbuf, nb, false, d_flag, s));   // R = Q_p^T W
+        opR.rows = m; opR.K = nb;
+        oR.rows = rest; oR.K = nb;
+        MPJ_TRY(oz_slice(Qp, 1, ldq, m, nb, &opR, s));          // rows of Q_p
+        MPJ_TRY(oz_slice(Rbuf, nb, 1, rest, nb, &oR, s));       // columns of R
+        MPJ_TRY(oz_gemm(opR, oR, -1.0, 1.0, W, ldq, false, d_flag, s));    // W -= Q_p R
+    }
+    return MPJ_SUCCESS;
+}
+
 // ---------------------------------------------------------------- no-allocation variant
 // mpj_mgs_noalloc runs the same blocked MGS as mpj_mgs but takes its scratch
 // (the panel projections R and their split partials, plus the rank flag) from

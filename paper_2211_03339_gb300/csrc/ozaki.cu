@@ -90,11 +90,12 @@ k_oz_slice_rows(const double* __restrict__ X, long long rs, int rows, int K, int
         slice_store(k < K ? ldexp(x[k], 7 - e) : 0.0, P, (size_t)pstride, (size_t)r * Kp + k);
 }
 
-// Rows strided: row r is X[r + k * ks] (the rows of a column-major matrix).  One
-// thread per row (reads coalesced across the threads of a warp).
+// Rows of a column-major matrix (row r is X[r + k * ks]), in two passes: the row
+// exponents (one thread per row; the reads of a warp are coalesced for each k),
+// then 32-row x 64-column tiles transposed through shared memory so that the
+// slice planes are written along k.
 __global__ void __launch_bounds__(128)
-k_oz_slice_strided(const double* __restrict__ X, long long ks, int rows, int K, int Kp,
-                   __nv_bfloat16* __restrict__ P, long long pstride, int* __restrict__ ex) {
+k_oz_rowexp_strided(const double* __restrict__ X, long long ks, int rows, int K, int* __restrict__ ex) {
     const int r = blockIdx.x * 128 + threadIdx.x;
     if (r >= rows) return;
     double m = 0.0;
@@ -102,9 +103,42 @@ k_oz_slice_strided(const double* __restrict__ X, long long ks, int rows, int K, 
     int e = 0;
     if (m > 0.0 && m <= 1.7976931348623157e308) frexp(m, &e);
     ex[r] = e;
-    for (int k = 0; k < Kp; ++k)
-        slice_store(k < K ? ldexp(X[(size_t)r + (size_t)k * ks], 7 - e) : 0.0, P, (size_t)pstride,
-                    (size_t)r * Kp + k);
+}
+
+__global__ void __launch_bounds__(256)
+k_oz_slice_tiled(const double* __restrict__ X, long long ks, int rows, int K, int Kp,
+                 __nv_bfloat16* __restrict__ P, long long pstride, const int* __restrict__ ex) {
+    __shared__ double tile[64][33];                          // [k][row]
+    const int r0 = blockIdx.x * 32, k0 = blockIdx.y * 64;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 32 * 64; i += 256) {
+        const int rr = i % 32, kk = i / 32;
+        const int r = r0 + rr, k = k0 + kk;
+        tile[kk][rr] = (r < rows && k < K) ? X[(size_t)r + (size_t)k * ks] : 0.0;
+    }
+    __syncthreads();
+    const int rr = tid / 8, kg = (tid % 8) * 8;              // 8 consecutive k per thread
+    const int r = r0 + rr;
+    if (r >= rows) return;
+    const int e = ex[r];
+    __nv_bfloat16 out[kS][8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        double a = ldexp(tile[kg + j][rr], 7 - e);
+#pragma unroll
+        for (int p = 0; p < kS; ++p) {
+            const double sl = rint(a);
+            out[p][j] = __float2bfloat16_rn((float)sl);
+            a = (a - sl) * 128.0;
+        }
+    }
+    const int kb = k0 + kg;
+    if (kb + 8 <= Kp) {
+#pragma unroll
+        for (int p = 0; p < kS; ++p)
+            *reinterpret_cast<uint4*>(P + p * (size_t)pstride + (size_t)r * Kp + kb) =
+                *reinterpret_cast<const uint4*>(out[p]);
+    }
 }
 
 // --------------------------------------------------------------- product
@@ -377,8 +411,9 @@ int oz_slice(const double* X, long long row_stride, long long k_stride, int rows
         if (k_stride == 1) {
             k_oz_slice_rows<<<rows, 128, 0, s>>>(X, row_stride, rows, K, Kp, op->planes, pstride, op->ex);
         } else {
-            k_oz_slice_strided<<<(rows + 127) / 128, 128, 0, s>>>(X, k_stride, rows, K, Kp, op->planes,
-                                                                  pstride, op->ex);
+            k_oz_rowexp_strided<<<(rows + 127) / 128, 128, 0, s>>>(X, k_stride, rows, K, op->ex);
+            dim3 g((rows + 31) / 32, (Kp + 63) / 64);
+            k_oz_slice_tiled<<<g, 256, 0, s>>>(X, k_stride, rows, K, Kp, op->planes, pstride, op->ex);
         }
     }
     MPJ_LAUNCH_CHECK("k_oz_slice");

@@ -305,3 +305,17 @@ def test_congruence_tensor_core_accuracy(mpj, n):
     bound = gn * (2 + gn) * (np.abs(Q).T @ np.abs(A) @ np.abs(Q))
     assert (np.abs(Tg - Tn) <= 2 * bound).all()
     assert np.linalg.norm(Tg - Tn) <= 4 * np.sqrt(n) * U * np.linalg.norm(A)
+
+
+def test_mgs_block_tensor_core_parity(mpj):
+    """n >= 1024 takes the block MGS (256-column panels, panel projections on the
+    tensor cores by exact splitting): same Q as the oracle's column MGS within
+    10 n u kappa(Z), orthonormal to working precision."""
+    m, n = 1300, 1100
+    rng = np.random.default_rng(m + n)
+    Z = rng.standard_normal((m, n))
+    Qo, Ro, rc = oracle.mgs(Z)
+    kappa = np.linalg.cond(Z)
+    Qg = host(mpj.mgs(dev(Z)))
+    assert np.abs(Qg - Qo).max() <= 10 * n * U * kappa
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(n)) <= 10 * n * U
