@@ -81,10 +81,17 @@ __device__ int pair_solve(Real* __restrict__ T, int N, int round, int pair, Real
     return applied;
 }
 
-// Double-float version of the off-diagonal tile update (Real = double only).
+// Double-float version of the off-diagonal tile update (Real = double only):
+// Y = X + D1 + D2 with D1 = X F_b and D2 = F_a^T (X + D1), both products in
+// double-float on the FP32 pipe.  X + D1 enters the second product as a
+// double-float sum (48 bits of X suffice there: it is multiplied by |F_a| <=
+// 2^-8), and D1 + D2 is added to the exact FP64 X once, so the FP64 pipe only
+// splits X and forms the final sum.  F comes from the precomputed float planes
+// when Fsplit is given (the grid engine), else it is split here (batched).
 template <int B>
 __device__ void apply_tile_df(double* T, int N, const double* __restrict__ Fbuf, int a, int b,
-                              int Ia, int Ja, int Ib, int Jb, float* smf) {
+                              int Ia, int Ja, int Ib, int Jb, float* smf,
+                              const float* __restrict__ Fsplit = nullptr) {
     constexpr int M = 2 * B;
     constexpr int LDSF = M + 4;
     constexpr int LDS = M + SmemPad<double>::value;
@@ -98,6 +105,8 @@ __device__ void apply_tile_df(double* T, int N, const double* __restrict__ Fbuf,
     float* Al = Ah + M * LDSF;
     const double* Fb = Fbuf + (size_t)b * M * M;
     const double* Fa = Fbuf + (size_t)a * M * M;
+    const float* Sb = Fsplit ? Fsplit + (size_t)b * 2 * M * M : nullptr;
+    const float* Sa = Fsplit ? Fsplit + (size_t)a * 2 * M * M : nullptr;
     double z[RM][RM];
 #pragma unroll
     for (int i = 0; i < RM; ++i)
@@ -110,30 +119,42 @@ __device__ void apply_tile_df(double* T, int N, const double* __restrict__ Fbuf,
         double v = T[(size_t)pair_global(r, Ia, Ja, B) + (size_t)pair_global(kc, Ib, Jb, B) * N];
         split_df(v, Xh[kc * LDSF + r], Xl[kc * LDSF + r]);
         int k = t / M, c = t % M;
-        split_df(Fb[t], Bh[k * LDSF + c], Bl[k * LDSF + c]);
-        split_df(Fa[t], Ah[k * LDSF + c], Al[k * LDSF + c]);
+        if (Fsplit) {
+            Bh[k * LDSF + c] = Sb[t]; Bl[k * LDSF + c] = Sb[M * M + t];
+            Ah[k * LDSF + c] = Sa[t]; Al[k * LDSF + c] = Sa[M * M + t];
+        } else {
+            split_df(Fb[t], Bh[k * LDSF + c], Bl[k * LDSF + c]);
+            split_df(Fa[t], Ah[k * LDSF + c], Al[k * LDSF + c]);
+        }
     }
     __syncthreads();
-    float ah[RM][RM], al[RM][RM];
-    tile_mm_df<M, LDSF>(Xh, Xl, Bh, Bl, ah, al);                  // X F_b
-#pragma unroll
-    for (int i = 0; i < RM; ++i)
-#pragma unroll
-        for (int j = 0; j < RM; ++j) z[i][j] += (double)ah[i][j] + (double)al[i][j];
+    float d1h[RM][RM], d1l[RM][RM];
+    tile_mm_df<M, LDSF>(Xh, Xl, Bh, Bl, d1h, d1l);                // D1 = X F_b
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < RM; ++j) {
-            int R = ty * RM + i, C = tx * RM + j;
-            split_df(z[i][j], Bh[R * LDSF + C], Bl[R * LDSF + C]);  // Z row-major
+            const int R = ty * RM + i, C = tx * RM + j;
+            float h, l;                                           // Z = X + D1 (double-float)
+            add_df(Xh[C * LDSF + R], Xl[C * LDSF + R], d1h[i][j], d1l[i][j], h, l);
+            Bh[R * LDSF + C] = h;                                 // Z row-major
+            Bl[R * LDSF + C] = l;
+            Xh[C * LDSF + R] = d1h[i][j];                         // park D1 over X (this
+            Xl[C * LDSF + R] = d1l[i][j];                         // thread's own entries)
         }
     __syncthreads();
-    tile_mm_df<M, LDSF>(Ah, Al, Bh, Bl, ah, al);                  // F_a^T Z
+    float d2h[RM][RM], d2l[RM][RM];
+    tile_mm_df<M, LDSF>(Ah, Al, Bh, Bl, d2h, d2l);                // D2 = F_a^T Z
 #pragma unroll
     for (int i = 0; i < RM; ++i)
 #pragma unroll
-        for (int j = 0; j < RM; ++j) z[i][j] += (double)ah[i][j] + (double)al[i][j];
+        for (int j = 0; j < RM; ++j) {
+            const int R = ty * RM + i, C = tx * RM + j;
+            float h, l;
+            add_df(Xh[C * LDSF + R], Xl[C * LDSF + R], d2h[i][j], d2l[i][j], h, l);
+            z[i][j] += (double)h + (double)l;                      // Y = X + (D1 + D2)
+        }
     __syncthreads();
     double* Ys = reinterpret_cast<double*>(smf);                  // col-major
     double* Yr = Ys + M * LDS;                                    // row-major
@@ -156,7 +177,7 @@ __device__ void apply_tile_df(double* T, int N, const double* __restrict__ Fbuf,
 template <class Real, int B>
 __device__ void apply_tile(Real* __restrict__ T, int N, const Real* __restrict__ Fbuf,
                            const float* __restrict__ fmax, int round, int a, int b, float df_gate,
-                           unsigned char* smraw) {
+                           unsigned char* smraw, const float* __restrict__ Fsplit = nullptr) {
     constexpr int M = 2 * B;
     constexpr int LDS = M + SmemPad<Real>::value;
     constexpr int RM = M / 16;
@@ -170,7 +191,7 @@ __device__ void apply_tile(Real* __restrict__ T, int N, const Real* __restrict__
     if constexpr (sizeof(Real) == 8) {
         if (fa <= df_gate && fb <= df_gate) {
             apply_tile_df<B>(reinterpret_cast<double*>(T), N, reinterpret_cast<const double*>(Fbuf),
-                             a, b, Ia, Ja, Ib, Jb, reinterpret_cast<float*>(smraw));
+                             a, b, Ia, Ja, Ib, Jb, reinterpret_cast<float*>(smraw), Fsplit);
             return;
         }
     }
@@ -214,7 +235,7 @@ __device__ void apply_tile(Real* __restrict__ T, int N, const Real* __restrict__
 template <class Real, int B>
 __device__ void apply_slab(Real* __restrict__ V, int N, const Real* __restrict__ Fbuf,
                            const float* __restrict__ fmax, int round, int rb, int b, float df_gate,
-                           unsigned char* smraw) {
+                           unsigned char* smraw, const float* __restrict__ Fsplit = nullptr) {
     constexpr int M = 2 * B;
     constexpr int LDS = M + SmemPad<Real>::value;
     const int nblocks = N / B;
@@ -226,7 +247,8 @@ __device__ void apply_slab(Real* __restrict__ V, int N, const Real* __restrict__
         if (fb <= df_gate) {
             right_multiply_rows_df<B>(reinterpret_cast<double*>(V), (size_t)N, N, rb * M, Ib, Jb,
                                       reinterpret_cast<const double*>(Fbuf) + (size_t)b * M * M,
-                                      reinterpret_cast<float*>(smraw));
+                                      reinterpret_cast<float*>(smraw),
+                                      Fsplit ? Fsplit + (size_t)b * 2 * M * M : nullptr);
             __syncthreads();
             return;
         }

@@ -122,6 +122,30 @@ __device__ __forceinline__ void split_df(double v, float& h, float& l) {
     l = __double2float_rn(v - (double)h);
 }
 
+// (h, l) = (ah, al) + (bh, bl) in double-float arithmetic (TwoSum of the high
+// parts, low parts added to the error, renormalised).
+__device__ __forceinline__ void add_df(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float s = __fadd_rn(ah, bh);
+    const float bb = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(bh, bb));
+    const float t = __fadd_rn(e, __fadd_rn(al, bl));
+    h = __fadd_rn(s, t);
+    l = __fsub_rn(t, __fsub_rn(h, s));
+}
+
+// Float planes of the block rotations F (row-major M x M per pair, hi plane then
+// lo plane), written once per round by the block solves so that the tile
+// kernels read them instead of splitting F in every tile.
+__device__ __forceinline__ void store_f_split(const double* F, int LD, int M, float* out) {
+    for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+        const int k = t / M, c = t % M;
+        float h, l;
+        split_df(F[c * LD + k], h, l);
+        out[t] = h;
+        out[M * M + t] = l;
+    }
+}
+
 // ah/al[i][j] = double-float sum_k A[k][ty*RM+i] * B[k][tx*RM+j] with the float
 // planes (Ah, Al), (Bh, Bl) laid out like tile_mm's operands (ld LDSF).
 template <int M, int LDSF>
@@ -176,7 +200,8 @@ __device__ __forceinline__ void split_tile(const double* D, float* H, float* L) 
 // X, which each thread reads into registers.  smem: 4 float planes of M*LDSF.
 template <int B>
 __device__ void right_multiply_rows_df(double* X, size_t ldx, int nrows, int row0, int Ib, int Jb,
-                                       const double* __restrict__ Fsrc, float* smf) {
+                                       const double* __restrict__ Fsrc, float* smf,
+                                       const float* __restrict__ Fsplit = nullptr) {
     constexpr int M = 2 * B;
     constexpr int LDSF = M + 4;
     constexpr int LDS = M + SmemPad<double>::value;
@@ -200,7 +225,12 @@ __device__ void right_multiply_rows_df(double* X, size_t ldx, int nrows, int row
         double v = gr < nrows ? X[(size_t)gr + (size_t)pair_global(kc, Ib, Jb, B) * ldx] : 0.0;
         split_df(v, Xh[kc * LDSF + r], Xl[kc * LDSF + r]);
         int k = t / M, c = t % M;
-        split_df(Fsrc[t], Fh[k * LDSF + c], Fl[k * LDSF + c]);     // Fsrc row-major
+        if (Fsplit) {                                              // precomputed planes
+            Fh[k * LDSF + c] = Fsplit[t];
+            Fl[k * LDSF + c] = Fsplit[M * M + t];
+        } else {
+            split_df(Fsrc[t], Fh[k * LDSF + c], Fl[k * LDSF + c]); // Fsrc row-major
+        }
     }
     __syncthreads();
     float ah[RM][RM], al[RM][RM];

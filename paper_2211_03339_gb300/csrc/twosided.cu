@@ -26,32 +26,39 @@ namespace mpj {
 template <class Real, int B>
 __global__ void __launch_bounds__(kSolveThreads)
 k_solve2(Real* __restrict__ T, int N, Real* __restrict__ Fbuf, float* __restrict__ fmax, int round,
-         Real eps, Real tau, Real gate, int max_inner, int cross, unsigned long long* __restrict__ rot_counter) {
+         Real eps, Real tau, Real gate, int max_inner, int cross, unsigned long long* __restrict__ rot_counter,
+         float* __restrict__ Fsplit) {
     constexpr int M = 2 * B;
     extern __shared__ __align__(16) unsigned char smraw[];
     int applied = pair_solve<Real, B>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
                                       Fbuf + (size_t)blockIdx.x * M * M, fmax + blockIdx.x, smraw, nullptr,
                                       cross ? round : -1);
     if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
+    if constexpr (sizeof(Real) == 8) {
+        // float planes of F for the double-float tile products (F is still in shared memory)
+        if (Fsplit)
+            store_f_split(reinterpret_cast<const double*>(smraw) + M * (M + 1), M + 1, M,
+                          Fsplit + (size_t)blockIdx.x * 2 * M * M);
+    }
 }
 
 template <class Real, int B>
 __global__ void __launch_bounds__(kThreads)
 k_apply2T(Real* __restrict__ T, int N, const Real* __restrict__ Fbuf, const float* __restrict__ fmax,
-          int round, float df_gate) {
+          int round, float df_gate, const float* __restrict__ Fsplit) {
     extern __shared__ __align__(16) unsigned char smraw[];
     int a, b;
     decode_tile(blockIdx.x, N / (2 * B), a, b);
-    apply_tile<Real, B>(T, N, Fbuf, fmax, round, a, b, df_gate, smraw);
+    apply_tile<Real, B>(T, N, Fbuf, fmax, round, a, b, df_gate, smraw, Fsplit);
 }
 
 template <class Real, int B>
 __global__ void __launch_bounds__(kThreads)
 k_apply2V(Real* __restrict__ V, int N, const Real* __restrict__ Fbuf, const float* __restrict__ fmax,
-          int round, float df_gate) {
+          int round, float df_gate, const float* __restrict__ Fsplit) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int K = N / (2 * B);
-    apply_slab<Real, B>(V, N, Fbuf, fmax, round, blockIdx.x / K, blockIdx.x % K, df_gate, smraw);
+    apply_slab<Real, B>(V, N, Fbuf, fmax, round, blockIdx.x / K, blockIdx.x % K, df_gate, smraw, Fsplit);
 }
 
 // Inner-sweep schedule of the block solves: the cross-pair schedule (inner_jacobi
@@ -86,6 +93,7 @@ size_t twosided_workspace_bytes(int N, int B) {
     a.take<double>(1024);
     a.take<double>(4);
     a.take<unsigned long long>(4);
+    if (sizeof(Real) == 8) a.take<float>((size_t)K * 2 * M * M);     // F split planes
     return a.used + 256;
 }
 
@@ -104,23 +112,24 @@ static int configure_twosided() {
 template <class Real, int B>
 static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r, Real eps, Real tau,
                         Real gate, float df_gate, int max_inner, unsigned long long* rot,
-                        cudaStream_t s) {
+                        float* Fsplit, cudaStream_t s) {
     constexpr int M = 2 * B;
     const int K = N / M;
     const bool dbl = sizeof(Real) == 8;
     { MPJ_PROF(dbl ? PC_SOLVE2_F64 : PC_SOLVE2_F32, s);
       k_solve2<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(T, N, Wbuf, fmax, r, eps, tau,
-                                                                         gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot); }
+                                                                         gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot,
+                                                                         Fsplit); }
     MPJ_LAUNCH_CHECK("k_solve2");
     int n_ttiles = K * (K - 1) / 2;
     if (n_ttiles > 0) {
         MPJ_PROF(dbl ? PC_APPLY2_F64 : PC_APPLY2_F32, s);
-        k_apply2T<Real, B><<<n_ttiles, kThreads, ApplySmem<Real, B>::t, s>>>(T, N, Wbuf, fmax, r, df_gate);
+        k_apply2T<Real, B><<<n_ttiles, kThreads, ApplySmem<Real, B>::t, s>>>(T, N, Wbuf, fmax, r, df_gate, Fsplit);
         MPJ_LAUNCH_CHECK("k_apply2T");
     }
     {
         MPJ_PROF(dbl ? PC_APPLY2V_F64 : PC_APPLY2V_F32, s);
-        k_apply2V<Real, B><<<(N / M) * K, kThreads, ApplySmem<Real, B>::v, s>>>(V, N, Wbuf, fmax, r, df_gate);
+        k_apply2V<Real, B><<<(N / M) * K, kThreads, ApplySmem<Real, B>::v, s>>>(V, N, Wbuf, fmax, r, df_gate, Fsplit);
         MPJ_LAUNCH_CHECK("k_apply2V");
     }
     return MPJ_SUCCESS;
@@ -139,7 +148,11 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     double* partial = ar.take<double>(1024);
     double* offv = ar.take<double>(4);
     unsigned long long* rot = ar.take<unsigned long long>(4);
-    if (!Wbuf || !fmax || !partial || !offv || !rot) { set_error_msg("workspace too small"); return MPJ_BAD_ARG; }
+    float* Fsplit = sizeof(Real) == 8 ? ar.take<float>((size_t)K * 2 * M * M) : nullptr;
+    if (!Wbuf || !fmax || !partial || !offv || !rot || (sizeof(Real) == 8 && !Fsplit)) {
+        set_error_msg("workspace too small");
+        return MPJ_BAD_ARG;
+    }
     HostScratch hs;
     MPJ_TRY(hs.init());
     const bool dbl = sizeof(Real) == 8;
@@ -182,10 +195,10 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
         for (int r = 0; r < rounds; ++r) {
             if (B == 16) {
                 MPJ_TRY((launch_round<Real, 16>(T, V, N, Wbuf, fmax, r, (Real)eps_skip, tau, gate,
-                                                df_gate, max_inner, rot, s)));
+                                                df_gate, max_inner, rot, Fsplit, s)));
             } else {
                 MPJ_TRY((launch_round<Real, 32>(T, V, N, Wbuf, fmax, r, (Real)eps_skip, tau, gate,
-                                                df_gate, max_inner, rot, s)));
+                                                df_gate, max_inner, rot, Fsplit, s)));
             }
         }
         MPJ_TRY(offnorm2(T, dbl, N, n, partial, offv, s));
