@@ -64,6 +64,28 @@ struct HostScratch {
     ~HostScratch();
 };
 
+// A second stream for the V updates of the sweep engines.  Round g uses buffer
+// set g & 1; the V update of round g runs on sv after the solve of round g
+// (event `solved`), and the solve of round g + 2 -- which rewrites that set --
+// waits for it (event `vdone`).  The destructor makes the main stream wait for
+// every V update (and the main stream) before anything later on it reads V.
+// The sweeps themselves run on `main`, a high-priority stream ordered after the
+// caller's stream, and the V updates on the low-priority `sv`, so that SM slots
+// freed by V tiles go to the next block solve (the critical path) first.
+struct SideStream {
+    cudaStream_t caller = nullptr, main = nullptr, sv = nullptr;
+    cudaEvent_t solved[2] = {nullptr, nullptr}, vdone[2] = {nullptr, nullptr};
+    cudaEvent_t start = nullptr, fin = nullptr;
+    bool pending[2] = {false, false};
+    int g = 0;
+    int init(cudaStream_t s);
+    int begin_round();          // returns the buffer set of this round, -1 on error
+    int after_solve();          // V stream waits for this round's solve
+    int after_v();              // marks this round's V update
+    void end_round() { ++g; }
+    ~SideStream();
+};
+
 // ---------------------------------------------------------------- profiling
 // Kernel classes counted (and, when enabled, timed with CUDA events on the
 // launching stream) by ProfScope; names in prof.cu.

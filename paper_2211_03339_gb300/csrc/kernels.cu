@@ -38,6 +38,63 @@ Workspace::~Workspace() {
     if (owned && ptr) cudaFreeAsync(ptr, stream);
 }
 
+int SideStream::init(cudaStream_t s) {
+    caller = s;
+    int lo = 0, hi = 0;                                   // numerically lower = higher priority
+    MPJ_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    MPJ_CUDA_TRY(cudaStreamCreateWithPriority(&main, cudaStreamNonBlocking, hi));
+    MPJ_CUDA_TRY(cudaStreamCreateWithPriority(&sv, cudaStreamNonBlocking, lo));
+    for (int i = 0; i < 2; ++i) {
+        MPJ_CUDA_TRY(cudaEventCreateWithFlags(&solved[i], cudaEventDisableTiming));
+        MPJ_CUDA_TRY(cudaEventCreateWithFlags(&vdone[i], cudaEventDisableTiming));
+    }
+    MPJ_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    MPJ_CUDA_TRY(cudaEventCreateWithFlags(&fin, cudaEventDisableTiming));
+    MPJ_CUDA_TRY(cudaEventRecord(start, caller));         // the sweeps follow the caller's work
+    MPJ_CUDA_TRY(cudaStreamWaitEvent(main, start, 0));
+    MPJ_CUDA_TRY(cudaStreamWaitEvent(sv, start, 0));
+    return MPJ_SUCCESS;
+}
+
+int SideStream::begin_round() {
+    const int set = g & 1;
+    if (pending[set] && cudaStreamWaitEvent(main, vdone[set], 0) != cudaSuccess) {
+        set_error("cudaStreamWaitEvent", cudaGetLastError());
+        return -1;
+    }
+    return set;
+}
+
+int SideStream::after_solve() {
+    const int set = g & 1;
+    MPJ_CUDA_TRY(cudaEventRecord(solved[set], main));
+    MPJ_CUDA_TRY(cudaStreamWaitEvent(sv, solved[set], 0));
+    return MPJ_SUCCESS;
+}
+
+int SideStream::after_v() {
+    const int set = g & 1;
+    MPJ_CUDA_TRY(cudaEventRecord(vdone[set], sv));
+    pending[set] = true;
+    return MPJ_SUCCESS;
+}
+
+SideStream::~SideStream() {
+    if (caller != main || caller != sv) {
+        for (int i = 0; i < 2; ++i)
+            if (pending[i]) cudaStreamWaitEvent(caller, vdone[i], 0);
+        if (main && fin && cudaEventRecord(fin, main) == cudaSuccess) cudaStreamWaitEvent(caller, fin, 0);
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (solved[i]) cudaEventDestroy(solved[i]);
+        if (vdone[i]) cudaEventDestroy(vdone[i]);
+    }
+    if (start) cudaEventDestroy(start);
+    if (fin) cudaEventDestroy(fin);
+    if (main) cudaStreamDestroy(main);
+    if (sv) cudaStreamDestroy(sv);
+}
+
 int HostScratch::init() {
     // one pinned block per thread, kept for the life of the process
     static thread_local char* blk = nullptr;

@@ -88,12 +88,14 @@ template <class Real>
 size_t twosided_workspace_bytes(int N, int B) {
     Arena a;
     int K = N / (2 * B), M = 2 * B;
-    a.take<Real>((size_t)K * M * M);
-    a.take<float>((size_t)K);
+    for (int set = 0; set < 2; ++set) {                 // block rotations of two consecutive rounds
+        a.take<Real>((size_t)K * M * M);
+        a.take<float>((size_t)K);
+        if (sizeof(Real) == 8) a.take<float>((size_t)K * 2 * M * M);   // F split planes
+    }
     a.take<double>(1024);
     a.take<double>(4);
     a.take<unsigned long long>(4);
-    if (sizeof(Real) == 8) a.take<float>((size_t)K * 2 * M * M);     // F split planes
     return a.used + 256;
 }
 
@@ -112,7 +114,8 @@ static int configure_twosided() {
 template <class Real, int B>
 static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r, Real eps, Real tau,
                         Real gate, float df_gate, int max_inner, unsigned long long* rot,
-                        float* Fsplit, cudaStream_t s) {
+                        float* Fsplit, cudaStream_t s, SideStream& side) {
+    cudaStream_t sv = side.sv;
     constexpr int M = 2 * B;
     const int K = N / M;
     const bool dbl = sizeof(Real) == 8;
@@ -121,6 +124,7 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
                                                                          gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot,
                                                                          Fsplit); }
     MPJ_LAUNCH_CHECK("k_solve2");
+    MPJ_TRY(side.after_solve());
     int n_ttiles = K * (K - 1) / 2;
     if (n_ttiles > 0) {
         MPJ_PROF(dbl ? PC_APPLY2_F64 : PC_APPLY2_F32, s);
@@ -128,10 +132,11 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
         MPJ_LAUNCH_CHECK("k_apply2T");
     }
     {
-        MPJ_PROF(dbl ? PC_APPLY2V_F64 : PC_APPLY2V_F32, s);
-        k_apply2V<Real, B><<<(N / M) * K, kThreads, ApplySmem<Real, B>::v, s>>>(V, N, Wbuf, fmax, r, df_gate, Fsplit);
+        MPJ_PROF(dbl ? PC_APPLY2V_F64 : PC_APPLY2V_F32, sv);
+        k_apply2V<Real, B><<<(N / M) * K, kThreads, ApplySmem<Real, B>::v, sv>>>(V, N, Wbuf, fmax, r, df_gate, Fsplit);
         MPJ_LAUNCH_CHECK("k_apply2V");
     }
+    MPJ_TRY(side.after_v());
     return MPJ_SUCCESS;
 }
 
@@ -143,18 +148,32 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     Arena ar;
     ar.base = static_cast<char*>(work);
     ar.size = twosided_workspace_bytes<Real>(N, B);
-    Real* Wbuf = ar.take<Real>((size_t)K * M * M);
-    float* fmax = ar.take<float>((size_t)K);
+    Real* Wbuf[2];
+    float* fmax[2];
+    float* Fsplit[2] = {nullptr, nullptr};
+    for (int set = 0; set < 2; ++set) {
+        Wbuf[set] = ar.take<Real>((size_t)K * M * M);
+        fmax[set] = ar.take<float>((size_t)K);
+        if (sizeof(Real) == 8) Fsplit[set] = ar.take<float>((size_t)K * 2 * M * M);
+    }
     double* partial = ar.take<double>(1024);
     double* offv = ar.take<double>(4);
     unsigned long long* rot = ar.take<unsigned long long>(4);
-    float* Fsplit = sizeof(Real) == 8 ? ar.take<float>((size_t)K * 2 * M * M) : nullptr;
-    if (!Wbuf || !fmax || !partial || !offv || !rot || (sizeof(Real) == 8 && !Fsplit)) {
+    if (!Wbuf[0] || !Wbuf[1] || !fmax[0] || !fmax[1] || !partial || !offv || !rot ||
+        (sizeof(Real) == 8 && (!Fsplit[0] || !Fsplit[1]))) {
         set_error_msg("workspace too small");
         return MPJ_BAD_ARG;
     }
     HostScratch hs;
     MPJ_TRY(hs.init());
+    // V is updated on a second stream: the V slabs of round r need only that round's
+    // block rotations, so they overlap the next block solves (which occupy K SMs).
+    // The rotations of two consecutive rounds are double buffered; the solve of
+    // round g + 2 waits until the V update of round g has read its buffers.  The
+    // rest runs on the side object's high-priority stream.
+    SideStream side;
+    MPJ_TRY(side.init(s));
+    s = side.main;
     const bool dbl = sizeof(Real) == 8;
     if (B == 16) { MPJ_TRY((configure_twosided<Real, 16>())); }
     else         { MPJ_TRY((configure_twosided<Real, 32>())); }
@@ -193,13 +212,16 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
         for (int r = 0; r < rounds; ++r) {
+            const int set = side.begin_round();
+            if (set < 0) return MPJ_CUDA_ERROR;
             if (B == 16) {
-                MPJ_TRY((launch_round<Real, 16>(T, V, N, Wbuf, fmax, r, (Real)eps_skip, tau, gate,
-                                                df_gate, max_inner, rot, Fsplit, s)));
+                MPJ_TRY((launch_round<Real, 16>(T, V, N, Wbuf[set], fmax[set], r, (Real)eps_skip, tau, gate,
+                                                df_gate, max_inner, rot, Fsplit[set], s, side)));
             } else {
-                MPJ_TRY((launch_round<Real, 32>(T, V, N, Wbuf, fmax, r, (Real)eps_skip, tau, gate,
-                                                df_gate, max_inner, rot, Fsplit, s)));
+                MPJ_TRY((launch_round<Real, 32>(T, V, N, Wbuf[set], fmax[set], r, (Real)eps_skip, tau, gate,
+                                                df_gate, max_inner, rot, Fsplit[set], s, side)));
             }
+            side.end_round();
         }
         MPJ_TRY(offnorm2(T, dbl, N, n, partial, offv, s));
         MPJ_CUDA_TRY(cudaMemcpyAsync(hs.d, offv, sizeof(double), cudaMemcpyDeviceToHost, s));
