@@ -66,7 +66,7 @@ typedef struct mpj_options {
     int    max_sweeps_stage1;  /* FP32 sweeps cap (default 40)                     */
     int    max_inner;          /* inner sweeps of each 2b x 2b block solve (default 1) */
     double tol_stage1;         /* step-1 stop: ||off(T32)||_F <= tol_stage1 ||A32||_F
-                                  (default 2^-24)                                  */
+                                  (default 2^-21, eight FP32 ulps)                 */
     double ju_ratio;           /* one-sided stop: sweep applies < ju_ratio*N rotations
                                   (default 2e-4, Sec. 6)                           */
     int    block;              /* block size b: 16 or 32 (0 = choose by n)         */

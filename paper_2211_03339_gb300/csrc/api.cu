@@ -19,7 +19,7 @@ constexpr double kUps = 5.9604644775390625e-08;  // 2^-24
 
 struct Opts {
     int max_sweeps = 40, max_sweeps1 = 40, max_inner = 1, block = 0;
-    double tol1 = kUps, ju_ratio = 2e-4;
+    double tol1 = 8 * kUps, ju_ratio = 2e-4;      // step-1 stop: 8 ulps of FP32 (see mpjacobi.h)
 };
 
 Opts read_opts(const mpj_options* o) {
