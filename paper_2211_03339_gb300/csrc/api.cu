@@ -257,7 +257,7 @@ int syevj_impl(bool mp, const double* A, int n, int lda, double* Lambda, double*
         MPJ_TRY(set_identity_f64(b.V64, N, N, N, s));
         tm.mark(1); tm.mark(2); tm.mark(3);
     }
-    MPJ_TRY(twosided_sweeps<double>(b.T64, b.V64, N, n, B, tol * normA, kU, op.max_sweeps,
+    MPJ_TRY(twosided_sweeps<double>(b.T64, b.V64, N, n, fp64_block(B), tol * normA, kU, op.max_sweeps,
                                     op.max_inner, b.eng, s, &r2));                          // step 4
     MPJ_TRY(diag_to_f64(b.T64, true, N, n, b.sc.d, s));
     MPJ_TRY(rank_sort(b.sc.d, 1, n, false, b.sc.perm, s));

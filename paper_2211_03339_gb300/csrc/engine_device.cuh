@@ -53,8 +53,8 @@ __device__ int pair_solve(Real* __restrict__ T, int N, int round, int pair, Real
     Real* F = S + M * LD;
     Real* G = F + M * LD;
     Real* cs = G + M * LD;
-    int* ip = reinterpret_cast<int*>(cs + 4 * (M / 2));
-    int* flag = ip + 3 * (M / 2) + 2;
+    int* ip = reinterpret_cast<int*>(cs + InnerLayout<Real, M>::kRealRot);
+    int* flag = ip + InnerLayout<Real, M>::kFlagOffset;
     const int nblocks = N / B;
     int I, J;
     round_pair(round, pair, nblocks, I, J);

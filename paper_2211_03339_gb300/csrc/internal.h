@@ -92,8 +92,8 @@ struct SideStream {
 enum ProfClass {
     PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
-    PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2V_F32,
-    PC_OZ_SLICE, PC_OZ_GEMM, kProfClasses
+    PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2_F32,
+    PC_OZ_SLICE, PC_OZ_GEMM, PC_TCV_F32, kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -110,6 +110,7 @@ bool trace_on();
 // ---------------------------------------------------------------- shapes
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 int choose_block(int n, const mpj_options* o);
+int fp64_block(int B);
 
 // ---------------------------------------------------------------- engines
 // Two-sided block Jacobi (Alg. 3.2 / step 4 of Alg. 4.1, parallel round-robin

@@ -40,13 +40,127 @@ template <class Real> __device__ __forceinline__ Real rabs(Real x) { return x < 
 
 // Shared-memory footprint of a block-pair solve for M = 2b: S, F and a third
 // M x (M+1) buffer (the Gram/correction matrix of the re-orthogonalisation),
-// c, s, c-1 of the M/2 rotations of a round, and pair indices / flags.
+// two buffers of c, s, c-1, t of the M/2 rotations of a step, two buffers of
+// pair indices and skip flags, a counter and two flags.  Carving: the Real
+// arrays start at `cs` (8 (M/2) values); the int arrays at ip = cs + 8 (M/2)
+// (6 (M/2) indices, then the counter at ip + 6 (M/2) and the caller's flags
+// at ip + 6 (M/2) + 2).
 template <class Real, int M>
 struct InnerLayout {
     static constexpr int LD = M + 1;
+    static constexpr int kRealRot = 8 * (M / 2);
+    static constexpr int kFlagOffset = 6 * (M / 2) + 2;
     static constexpr size_t bytes =
-        sizeof(Real) * (3 * M * LD + 4 * (M / 2)) + sizeof(int) * (3 * (M / 2) + 8);
+        sizeof(Real) * (3 * M * LD + kRealRot) + sizeof(int) * (6 * (M / 2) + 8);
 };
+
+// Rotations of step r of an inner sweep (warp 0): pair (p, q) of lane `tid`, its
+// (c, s, c - 1, t) or the identity when skipped, into one buffer of the step
+// arrays.  Returns the number of rotations of the step (all lanes of warp 0).
+template <class Real, int M>
+__device__ __forceinline__ int step_rotations(const Real* S, Real* cs, int* ip, int r, int cross_round, Real eps,
+                                              Real tau) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    const int tid = threadIdx.x;
+    int mine = 0;
+    if (tid < P) {
+        int p, q;
+        if (cross_round < 0) {
+            p = rr_index(r, tid, M);
+            q = rr_index(r, M - 1 - tid, M);
+        } else if (r < P) {
+            p = tid;
+            q = P + (tid + r) % P;
+        } else {
+            const int qr = cross_round % (P - 1), h = tid / (P / 2), i = tid % (P / 2);
+            p = h * P + rr_index(qr, i, P);
+            q = h * P + rr_index(qr, P - 1 - i, P);
+        }
+        if (p > q) { int t = p; p = q; q = t; }
+        Real apq = S[q * LD + p], app = S[p * LD + p], aqq = S[q * LD + q];
+        Real c = Real(1), s = Real(0), t = Real(0);
+        int skip = 1;
+        Real aa = rabs(apq);
+        if (apq != Real(0) && aa > tau && !(aa <= eps * sqrt(rabs(app * aqq)))) {
+            rotation_cs(app, aqq, apq, c, s, t);
+            skip = 0;
+        }
+        cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = -(s * s) / (Real(1) + c); cs[3 * P + tid] = t;
+        ip[tid] = p; ip[P + tid] = q; ip[2 * P + tid] = skip;
+        mine = !skip;
+    }
+    return __popc(__ballot_sync(0xffffffffu, mine));
+}
+
+// Two-sided update of S by the rotations of one step buffer: the 2x2 blocks
+// (a, b), a <= b, mirrored below the diagonal.
+template <class Real, int M>
+__device__ __forceinline__ void step_update_s(Real* S, const Real* cs, const int* ip) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    const Real* sn = cs + P;
+    const Real* tt = cs + 3 * P;
+    const int* iq = ip + P;
+    const int* sk = ip + 2 * P;
+    for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+        int a = t / P, b = t % P;
+        if (a > b) continue;
+        int pa = ip[a], qa = iq[a];
+        Real ca = cs[a], sa = sn[a];
+        if (a == b) {
+            // b_pp = c^2 a_pp - 2 s c a_pq + s^2 a_qq and b_qq = s^2 a_pp + 2 s c a_pq
+            // + c^2 a_qq reduce, for the (c, s) of Lemma 3.1, to a_pp - t a_pq and
+            // a_qq + t a_pq: one rounding of a small correction instead of three
+            // rounded products of the full diagonal entries.
+            Real apq = S[qa * LD + pa], ta = tt[a];
+            S[pa * LD + pa] = S[pa * LD + pa] - ta * apq;
+            S[qa * LD + qa] = S[qa * LD + qa] + ta * apq;
+            S[qa * LD + pa] = Real(0);
+            S[pa * LD + qa] = Real(0);
+        } else {
+            if (sk[a] && sk[b]) continue;     // both rotations are the identity
+            int pb = ip[b], qb = iq[b];
+            Real cb = cs[b], sb = sn[b];
+            Real x00 = S[pb * LD + pa], x01 = S[qb * LD + pa];
+            Real x10 = S[pb * LD + qa], x11 = S[qb * LD + qa];
+            // rows: J_a^T X
+            Real y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+            Real y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+            // columns: (J_a^T X) J_b
+            Real z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
+            Real z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
+            S[pb * LD + pa] = z00; S[qb * LD + pa] = z01;
+            S[pb * LD + qa] = z10; S[qb * LD + qa] = z11;
+            S[pa * LD + pb] = z00; S[pa * LD + qb] = z01;
+            S[qa * LD + pb] = z10; S[qa * LD + qb] = z11;
+        }
+    }
+}
+
+// F <- F J + (J - I) for the rotations of one step buffer (columns p, q of every
+// rotation), by the threads t0, t0 + nt, ... (t0 = this thread's index among them).
+template <class Real, int M>
+__device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int* ip, int t0, int nt) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    const Real* sn = cs + P;
+    const Real* cm = cs + 2 * P;
+    const int* iq = ip + P;
+    const int* sk = ip + 2 * P;
+    for (int t = t0; t < M * P; t += nt) {
+        int row = t % M, a = t / M;
+        if (sk[a]) continue;
+        int pa = ip[a], qa = iq[a];
+        Real c = cs[a], s = sn[a];
+        Real fp = F[pa * LD + row], fq = F[qa * LD + row];
+        Real np = c * fp - s * fq, nq = s * fp + c * fq;
+        if (row == pa) { np += cm[a]; nq += s; }
+        else if (row == qa) { np -= s; nq += cm[a]; }
+        F[pa * LD + row] = np;
+        F[qa * LD + row] = nq;
+    }
+}
 
 // Cyclic Jacobi on the symmetric M x M matrix S (shared, column-major, ld M+1).
 // The accumulated rotation W = J_1 J_2 ... is kept as F = W - I (F must hold
@@ -64,102 +178,37 @@ struct InnerLayout {
 // step over pairs inside each block (round cross_round mod (M/2 - 1) of the
 // tournament over that block), so that over the rounds of an outer sweep every
 // intra-block pair is still visited.
+// Software pipeline: the rotations of a step depend only on S after the
+// previous step, not on F, so warp 0 forms those of step r + 1 (the serial
+// chain of divisions and square roots) while the other warps accumulate
+// step r into F; the step arrays are double buffered.
 template <class Real, int M>
 __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real tau, int max_inner,
                             int cross_round = -1) {
-    constexpr int LD = M + 1;
     constexpr int P = M / 2;
     static_assert(P <= 32, "pair count must fit one warp");
-    Real* sn = cs + P;
-    Real* cm = sn + P;               // c - 1 = -s^2 / (1 + c)
-    Real* tt = cm + P;               // t = s / c
-    int* iq = ip + P;
-    int* sk = iq + P;
-    volatile int* cnt = sk + P;      // [0] applied in this sweep
+    volatile int* cnt = ip + 6 * P;  // [0] applied in this sweep
     const int tid = threadIdx.x;
+    const int nsteps = cross_round >= 0 ? P + 1 : M - 1;
     int total = 0;
     for (int sweep = 0; sweep < max_inner; ++sweep) {
         int applied = 0;
-        const int nsteps = cross_round >= 0 ? P + 1 : M - 1;
+        if (tid < 32) applied += step_rotations<Real, M>(S, cs, ip, 0, cross_round, eps, tau);
+        __syncthreads();
         for (int r = 0; r < nsteps; ++r) {
-            if (tid < 32) {
-                int mine = 0;
-                if (tid < P) {
-                    int p, q;
-                    if (cross_round < 0) {
-                        p = rr_index(r, tid, M);
-                        q = rr_index(r, M - 1 - tid, M);
-                    } else if (r < P) {
-                        p = tid;
-                        q = P + (tid + r) % P;
-                    } else {
-                        const int qr = cross_round % (P - 1), h = tid / (P / 2), i = tid % (P / 2);
-                        p = h * P + rr_index(qr, i, P);
-                        q = h * P + rr_index(qr, P - 1 - i, P);
-                    }
-                    if (p > q) { int t = p; p = q; q = t; }
-                    Real apq = S[q * LD + p], app = S[p * LD + p], aqq = S[q * LD + q];
-                    Real c = Real(1), s = Real(0), t = Real(0);
-                    int skip = 1;
-                    Real aa = rabs(apq);
-                    if (apq != Real(0) && aa > tau && !(aa <= eps * sqrt(rabs(app * aqq)))) {
-                        rotation_cs(app, aqq, apq, c, s, t);
-                        skip = 0;
-                    }
-                    cs[tid] = c; sn[tid] = s; cm[tid] = -(s * s) / (Real(1) + c); tt[tid] = t;
-                    ip[tid] = p; iq[tid] = q; sk[tid] = skip;
-                    mine = !skip;
-                }
-                applied += __popc(__ballot_sync(0xffffffffu, mine));
-            }
+            const int cur = r & 1;
+            Real* csc = cs + cur * 4 * P;
+            int* ipc = ip + cur * 3 * P;
+            step_update_s<Real, M>(S, csc, ipc);
             __syncthreads();
-            // two-sided update of the 2x2 blocks (a, b), a <= b, mirrored below the diagonal
-            for (int t = tid; t < P * P; t += blockDim.x) {
-                int a = t / P, b = t % P;
-                if (a > b) continue;
-                int pa = ip[a], qa = iq[a];
-                Real ca = cs[a], sa = sn[a];
-                if (a == b) {
-                    // b_pp = c^2 a_pp - 2 s c a_pq + s^2 a_qq and b_qq = s^2 a_pp + 2 s c a_pq
-                    // + c^2 a_qq reduce, for the (c, s) of Lemma 3.1, to a_pp - t a_pq and
-                    // a_qq + t a_pq: one rounding of a small correction instead of three
-                    // rounded products of the full diagonal entries.
-                    Real apq = S[qa * LD + pa], ta = tt[a];
-                    S[pa * LD + pa] = S[pa * LD + pa] - ta * apq;
-                    S[qa * LD + qa] = S[qa * LD + qa] + ta * apq;
-                    S[qa * LD + pa] = Real(0);
-                    S[pa * LD + qa] = Real(0);
-                } else {
-                    if (sk[a] && sk[b]) continue;     // both rotations are the identity
-                    int pb = ip[b], qb = iq[b];
-                    Real cb = cs[b], sb = sn[b];
-                    Real x00 = S[pb * LD + pa], x01 = S[qb * LD + pa];
-                    Real x10 = S[pb * LD + qa], x11 = S[qb * LD + qa];
-                    // rows: J_a^T X
-                    Real y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
-                    Real y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
-                    // columns: (J_a^T X) J_b
-                    Real z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
-                    Real z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
-                    S[pb * LD + pa] = z00; S[qb * LD + pa] = z01;
-                    S[pb * LD + qa] = z10; S[qb * LD + qa] = z11;
-                    S[pa * LD + pb] = z00; S[pa * LD + qb] = z01;
-                    S[qa * LD + pb] = z10; S[qa * LD + qb] = z11;
-                }
-            }
-            // F <- F J + (J - I): columns p, q of every rotation
-            for (int t = tid; t < M * P; t += blockDim.x) {
-                int row = t % M, a = t / M;
-                if (sk[a]) continue;
-                int pa = ip[a], qa = iq[a];
-                Real c = cs[a], s = sn[a];
-                Real fp = F[pa * LD + row], fq = F[qa * LD + row];
-                Real np = c * fp - s * fq, nq = s * fp + c * fq;
-                if (row == pa) { np += cm[a]; nq += s; }
-                else if (row == qa) { np -= s; nq += cm[a]; }
-                F[pa * LD + row] = np;
-                F[qa * LD + row] = nq;
-            }
+            const bool more = r + 1 < nsteps;
+            if (more && tid < 32)
+                applied += step_rotations<Real, M>(S, cs + (cur ^ 1) * 4 * P, ip + (cur ^ 1) * 3 * P, r + 1,
+                                                   cross_round, eps, tau);
+            else if (more)
+                step_update_f<Real, M>(F, csc, ipc, tid - 32, blockDim.x - 32);
+            else
+                step_update_f<Real, M>(F, csc, ipc, tid, blockDim.x);
             __syncthreads();
         }
         if (tid == 0) cnt[0] = applied;

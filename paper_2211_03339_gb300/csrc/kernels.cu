@@ -3,6 +3,7 @@
 // host-side workspace and error plumbing.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.h"
@@ -111,6 +112,16 @@ HostScratch::~HostScratch() {}
 int choose_block(int n, const mpj_options* o) {
     if (o && (o->block == 16 || o->block == 32)) return o->block;
     return n <= 256 ? 16 : 32;
+}
+
+// Block size of the FP64 sweeps of the EVD: the stage-1 size B unless
+// MPJ_B64=16 asks for b = 16 there (N stays a multiple of 2B, so of 32).
+int fp64_block(int B) {
+    static const int forced = [] {
+        const char* e = std::getenv("MPJ_B64");
+        return e && std::atoi(e) == 16 ? 16 : 0;
+    }();
+    return forced ? forced : B;
 }
 
 // ------------------------------------------------------------------ copies

@@ -12,6 +12,7 @@
 // projections, W = W - Q_p (Q_p^T W), as two FP64 GEMMs (block MGS).
 #include <cooperative_groups.h>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 
 #include "internal.h"
@@ -78,6 +79,144 @@ k_mgs_panel(double* __restrict__ Q, int m, int ldq, int j0, int pb, int* __restr
         __syncthreads();                // own rows updated before the next column's dots
     }
     cluster.sync();                     // no CTA leaves while others may read its part[]
+}
+
+// Shared-memory resident panel MGS: the same column MGS, by a cluster of 8 or
+// 16 CTAs, each holding its `rows_per` rows of the 32-column panel in shared
+// memory (column-major, ld rows_per; rows past m are zero) from the first
+// column to the last, so every column costs only shared-memory traffic, one
+// cluster barrier and the FP64 arithmetic of its dots and updates.  After the
+// cluster-wide sums, warp 0 forms r_jj, 1/r_jj and the update coefficients
+// -r_jk/r_jj once for the CTA.
+__global__ void __launch_bounds__(kThreads)
+k_mgs_panel_smem(double* __restrict__ Q, int m, int ldq, int j0, int pb, int rows_per,
+                 int* __restrict__ flag) {
+    extern __shared__ __align__(16) double Ps[];
+    __shared__ double part[2][PB];
+    __shared__ double coef[PB];
+    __shared__ double sinv;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    const int ncl = (int)cluster.num_blocks();
+    const int r0 = rank * rows_per;
+    const int nr = max(0, min(m, r0 + rows_per) - r0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int NW = kThreads / 32;
+    double* P = Q + (size_t)j0 * ldq + r0;
+    for (int t = threadIdx.x; t < pb * rows_per; t += kThreads) {
+        const int k = t / rows_per, rr = t - k * rows_per;
+        Ps[t] = rr < nr ? P[(size_t)k * ldq + rr] : 0.0;
+    }
+    __syncthreads();
+    for (int jj = 0; jj < pb; ++jj) {
+        const int buf = jj & 1;
+        const double* wj = Ps + (size_t)jj * rows_per;
+        for (int k = jj + warp; k < pb; k += NW) {
+            const double* wk = Ps + (size_t)k * rows_per;
+            double sacc = 0.0;
+            for (int rr = lane; rr < rows_per; rr += 32) sacc = fma(wj[rr], wk[rr], sacc);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) part[buf][k] = sacc;
+        }
+        cluster.sync();                 // partials of this column visible cluster-wide
+        if (warp == 0) {
+            const int k = lane;
+            double g = 0.0;
+            if (k >= jj && k < pb)
+                for (int c = 0; c < ncl; ++c) g += cluster.map_shared_rank(&part[buf][0], c)[k];
+            const double gjj = __shfl_sync(0xffffffffu, g, jj);
+            const double rjj = sqrt(gjj);
+            if ((rjj == 0.0 || !(rjj == rjj)) && lane == 0 && rank == 0) atomicOr(flag, 1);
+            const double inv = rjj > 0.0 ? 1.0 / rjj : 0.0;
+            coef[k] = -(g * inv);
+            if (lane == 0) sinv = inv;
+        }
+        __syncthreads();
+        const double inv = sinv;
+        // q_j = w_j / r_jj ; w_k -= (r_jk / r_jj) q_j for k > jj
+        for (int rr = threadIdx.x; rr < rows_per; rr += kThreads) {
+            const double q = Ps[(size_t)jj * rows_per + rr] * inv;
+            Ps[(size_t)jj * rows_per + rr] = q;
+            for (int k = jj + 1; k < pb; ++k)
+                Ps[(size_t)k * rows_per + rr] = fma(coef[k], q, Ps[(size_t)k * rows_per + rr]);
+        }
+        __syncthreads();                // own rows updated before the next column's dots
+    }
+    for (int t = threadIdx.x; t < pb * rows_per; t += kThreads) {
+        const int k = t / rows_per, rr = t - k * rows_per;
+        if (rr < nr) P[(size_t)k * ldq + rr] = Ps[t];
+    }
+    cluster.sync();                     // no CTA leaves while others may read its part[]
+}
+
+constexpr size_t kPanelSmemMax = 200 * 1024;
+
+// Cluster size for k_mgs_panel_smem on the current device: 16 CTAs when the
+// device can run such a cluster with `smem` bytes each (non-portable size), else 8;
+// 0 when neither fits.  Cached per device and shared-memory size class.
+static int panel_cluster_size(size_t smem) {
+    constexpr int kDev = 64;
+    static std::mutex mu;
+    static int cache[kDev][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) return 0;
+    const int cls = smem > 100 * 1024 ? 1 : 0;      // sizes are probed at the class maximum
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache[dev][cls]) return cache[dev][cls] > 0 ? cache[dev][cls] : 0;
+    const size_t probe = cls ? kPanelSmemMax : 100 * 1024;
+    int best = -1;
+    if (cudaFuncSetAttribute(k_mgs_panel_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelSmemMax) ==
+            cudaSuccess &&
+        cudaFuncSetAttribute(k_mgs_panel_smem, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+        for (int cl : {16, 8}) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cl; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(cl); cfg.blockDim = dim3(kThreads); cfg.dynamicSmemBytes = probe;
+            cfg.attrs = at; cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, k_mgs_panel_smem, &cfg) == cudaSuccess && nclusters > 0) {
+                best = cl;
+                break;
+            }
+        }
+    }
+    cudaGetLastError();                 // a refused probe leaves no sticky error
+    cache[dev][cls] = best;
+    return best > 0 ? best : 0;
+}
+
+// One 32-column panel: the shared-memory kernel when the panel's rows fit the
+// cluster's shared memory, else the global-memory kernel.
+static int mgs_panel(double* Q, int m, int ldq, int j0, int pb, int* d_flag, cudaStream_t s) {
+    static const bool smem_off = [] { const char* e = std::getenv("MPJ_MGS_SMEM"); return e && *e == '0'; }();
+    int cl = 0;
+    int rows_per = 0;
+    size_t smem = 0;
+    if (!smem_off) {
+        for (int c : {16, 8}) {
+            rows_per = (m + c - 1) / c;
+            smem = sizeof(double) * (size_t)rows_per * PB;
+            if (smem <= kPanelSmemMax && panel_cluster_size(smem) >= c) { cl = c; break; }
+        }
+    }
+    if (cl) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cl; at[0].val.clusterDim.y = 1; at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(cl); cfg.blockDim = dim3(kThreads); cfg.dynamicSmemBytes = smem;
+        cfg.stream = s; cfg.attrs = at; cfg.numAttrs = 1;
+        MPJ_PROF(PC_MGS_PANEL, s);
+        MPJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_mgs_panel_smem, Q, m, ldq, j0, pb, rows_per, d_flag));
+        return MPJ_SUCCESS;
+    }
+    { MPJ_PROF(PC_MGS_PANEL, s);
+      k_mgs_panel<<<CL, kThreads, 0, s>>>(Q, m, ldq, j0, pb, d_flag); }
+    MPJ_LAUNCH_CHECK("k_mgs_panel");
+    return MPJ_SUCCESS;
 }
 
 // Panel projections R = Q_p^T W (pb x rest, K = m rows): the contraction is
@@ -157,9 +296,7 @@ int mgs_inplace(double* Q, int m, int n, int ldq, void* work, int* d_flag, cudaS
     const int ksplit = ksplit_for(m);
     for (int j0 = 0; j0 < n; j0 += PB) {
         int pb = (n - j0) < PB ? (n - j0) : PB;
-        { MPJ_PROF(PC_MGS_PANEL, s);
-    k_mgs_panel<<<CL, kThreads, 0, s>>>(Q, m, ldq, j0, pb, d_flag); }
-        MPJ_LAUNCH_CHECK("k_mgs_panel");
+        MPJ_TRY(mgs_panel(Q, m, ldq, j0, pb, d_flag, s));
         int rest = n - j0 - pb;
         if (rest > 0) {
             const double* Qp = Q + (size_t)j0 * ldq;

@@ -131,8 +131,8 @@ k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
     Real* F = S + M * LD;
     Real* G2 = F + M * LD;
     Real* cs = G2 + M * LD;
-    int* ip = reinterpret_cast<int*>(cs + 4 * (M / 2));
-    int* flag = ip + 3 * (M / 2) + 2;
+    int* ip = reinterpret_cast<int*>(cs + InnerLayout<Real, M>::kRealRot);
+    int* flag = ip + InnerLayout<Real, M>::kFlagOffset;
     const size_t off = (size_t)blockIdx.x * nsplit * M * M;
     for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
         int r = t % M, c = t / M;

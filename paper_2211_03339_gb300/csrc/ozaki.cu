@@ -180,7 +180,7 @@ __device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
 __global__ void __launch_bounds__(192, 1)
 k_oz_gemm(const __grid_constant__ OzMaps maps, const int* __restrict__ exA, const int* __restrict__ exB,
           double* __restrict__ C, int ldc, int M, int N, int K, double alpha, double beta, int nM, int nN,
-          int* __restrict__ err) {
+          int upper_only, int* __restrict__ err) {
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                                          ~uintptr_t(1023));
@@ -194,6 +194,8 @@ k_oz_gemm(const __grid_constant__ OzMaps maps, const int* __restrict__ exA, cons
     const int gsz = nM - m0 < 8 ? nM - m0 : 8;
     const int local = id % (8 * nN);
     const int mt = m0 + local % gsz, nt = local / gsz;
+    // a tile strictly below the diagonal is not needed when the caller mirrors the upper triangle
+    if (upper_only && nt * kTN + kTN - 1 < mt * kTM) return;
     const int nk = (K + kKS - 1) / kKS;
     const int nkb = (nk + kKB - 1) / kKB;
     if (tid == 0) {
@@ -427,15 +429,13 @@ int oz_gemm(const OzOperand& A, const OzOperand& B, double alpha, double beta, d
     OzMaps maps;
     MPJ_TRY(encode_planes(&maps.a, A.planes, K, round_up(K, 8), M, kTM));
     MPJ_TRY(encode_planes(&maps.b, B.planes, K, round_up(K, 8), N, kTN));
-    static bool configured = false;
-    if (!configured) {
-        MPJ_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem));
-        configured = true;
-    }
+    MPJ_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem));
+    const int upper_only = upper_mirror && M == N ? 1 : 0;
     const int nM = (M + kTM - 1) / kTM, nN = (N + kTN - 1) / kTN;
     {
         MPJ_PROF(PC_OZ_GEMM, s);
-        k_oz_gemm<<<nM * nN, 192, kGemmSmem, s>>>(maps, A.ex, B.ex, C, ldc, M, N, K, alpha, beta, nM, nN, d_flag);
+        k_oz_gemm<<<nM * nN, 192, kGemmSmem, s>>>(maps, A.ex, B.ex, C, ldc, M, N, K, alpha, beta, nM, nN, upper_only,
+                                                       d_flag);
     }
     MPJ_LAUNCH_CHECK("k_oz_gemm");
     if (upper_mirror && M == N) {

@@ -412,7 +412,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
             }
             MPJ_LAUNCH_CHECK("k_pass_tc pass 1");
             {
-                MPJ_PROF(PC_TC2V_F32, s);
+                MPJ_PROF(PC_TC2_F32, s);
                 k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps2[set], T, N, n_slabs, items, items, Sbuf[set],
                                                                fmax[set], r, rot + 1);
             }
@@ -422,7 +422,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
                 // for N >= 8192, where the SM slots then free up tile by tile for the next
                 // block solve on the high-priority stream (measured: 273 vs 284 ms of
                 // step 1 at n = 4096, 1443 vs 1352 ms at n = 8192).
-                MPJ_PROF(PC_TC2V_F32, side.sv);
+                MPJ_PROF(PC_TCV_F32, side.sv);
                 k_pass_tc<<<gridv, kTcThreads, kPassSmem, side.sv>>>(maps2[set], T, N, n_slabs, 0, items, nullptr,
                                                                      fmax[set], r, rot + 1);
             }

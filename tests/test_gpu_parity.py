@@ -75,6 +75,20 @@ def test_mgs_parity_general(mpj, m, n):
     assert np.abs(Qg - Qo).max() <= 10 * n * U * kappa
 
 
+@pytest.mark.parametrize("m,n", [(6500, 45), (13000, 40)])
+def test_mgs_parity_tall(mpj, m, n):
+    """Tall panels: up to 12800 rows a 32-column panel is held in the shared memory
+    of a 16-CTA cluster (more than 400 rows per CTA from 6401 rows on); beyond
+    that the panel kernel works from global memory.  Both against the oracle."""
+    rng = np.random.default_rng(m + n)
+    Z = rng.standard_normal((m, n))
+    Qo, Ro, rc = oracle.mgs(Z)
+    kappa = np.linalg.cond(Z)
+    Qg = host(mpj.mgs(dev(Z)))
+    assert np.abs(Qg - Qo).max() <= 10 * n * U * kappa
+    assert np.linalg.norm(Qg.T @ Qg - np.eye(n)) <= 10 * n * U
+
+
 @pytest.mark.parametrize("n", [17, 64, 129, 300])
 def test_congruence_parity(mpj, n):
     A, _ = synth.sym_matrix(n, "uniform", seed=200 + n)
