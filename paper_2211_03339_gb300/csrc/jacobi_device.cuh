@@ -93,19 +93,34 @@ __device__ __forceinline__ int step_rotations(const Real* S, Real* cs, int* ip, 
     return __popc(__ballot_sync(0xffffffffu, mine));
 }
 
+// Work items of the two-sided S update, u in [0, P(P+1)/2): the P diagonal 2x2
+// blocks first (u < P, a = b = u), then the strictly upper blocks (a < b) row by
+// row.  Enumerating only a <= b keeps whole warps on the same branch, so the
+// FP64 pipe is not spent on masked-off lanes.  Packed as a | b << 8, -1 past
+// the end.  Each thread keeps its (at most three) items for the whole solve.
+template <int P>
+__device__ __forceinline__ int upper_item(int u) {
+    if (u >= P * (P + 1) / 2) return -1;
+    if (u < P) return u | (u << 8);
+    int v = u - P, a = 0;
+    while (v >= P - 1 - a) { v -= P - 1 - a; ++a; }
+    return a | ((a + 1 + v) << 8);
+}
+
 // Two-sided update of S by the rotations of one step buffer: the 2x2 blocks
-// (a, b), a <= b, mirrored below the diagonal.
+// (a, b), a <= b, of this thread's items, mirrored below the diagonal.
 template <class Real, int M>
-__device__ __forceinline__ void step_update_s(Real* S, const Real* cs, const int* ip) {
+__device__ __forceinline__ void step_update_s(Real* S, const Real* cs, const int* ip, const int (&items)[3]) {
     constexpr int LD = M + 1;
     constexpr int P = M / 2;
     const Real* sn = cs + P;
     const Real* tt = cs + 3 * P;
     const int* iq = ip + P;
     const int* sk = ip + 2 * P;
-    for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
-        int a = t / P, b = t % P;
-        if (a > b) continue;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (items[k] < 0) continue;
+        const int a = items[k] & 255, b = items[k] >> 8;
         int pa = ip[a], qa = iq[a];
         Real ca = cs[a], sa = sn[a];
         if (a == b) {
@@ -172,7 +187,8 @@ __device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int
 // (Remark 3.7) or |s_pq| <= tau (entries that cannot matter for the stopping
 // test).  Stops after an inner sweep with no rotation or after max_inner
 // sweeps.  Returns the number of rotations applied (all threads).
-// Must be called by all threads of the block (any multiple of 32, at least 256).
+// Must be called by all threads of the block (any multiple of 32, at least 256,
+// so that three S-update items per thread cover the P(P+1)/2 <= 528 blocks).
 // With cross_round >= 0 an inner sweep is the M/2 steps that rotate every pair
 // (i, j) with i in the first block and j in the second once, followed by one
 // step over pairs inside each block (round cross_round mod (M/2 - 1) of the
@@ -190,6 +206,9 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
     volatile int* cnt = ip + 6 * P;  // [0] applied in this sweep
     const int tid = threadIdx.x;
     const int nsteps = cross_round >= 0 ? P + 1 : M - 1;
+    int items[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) items[k] = upper_item<P>(tid + k * (int)blockDim.x);
     int total = 0;
     for (int sweep = 0; sweep < max_inner; ++sweep) {
         int applied = 0;
@@ -199,7 +218,7 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
             const int cur = r & 1;
             Real* csc = cs + cur * 4 * P;
             int* ipc = ip + cur * 3 * P;
-            step_update_s<Real, M>(S, csc, ipc);
+            step_update_s<Real, M>(S, csc, ipc, items);
             __syncthreads();
             const bool more = r + 1 < nsteps;
             if (more && tid < 32)

@@ -114,6 +114,15 @@ int choose_block(int n, const mpj_options* o) {
     return n <= 256 ? 16 : 32;
 }
 
+// Dynamic shared memory of a block-solve launch: `need`, or 160 KB when
+// MPJ_SOLVE_EXCL=1, so that no tile-update CTA of the side stream (70-96 KB)
+// fits beside a solve CTA on its SM.
+size_t solve_smem(size_t need) {
+    static const bool excl = [] { const char* e = std::getenv("MPJ_SOLVE_EXCL"); return e && *e == '1'; }();
+    const size_t x = 160 * 1024;
+    return excl && need < x ? x : need;
+}
+
 // Block size of the FP64 sweeps of the EVD: the stage-1 size B unless
 // MPJ_B64=16 asks for b = 16 there (N stays a multiple of 2B, so of 32).
 int fp64_block(int B) {

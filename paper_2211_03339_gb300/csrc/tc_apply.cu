@@ -360,7 +360,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     HostScratch hs;
     MPJ_TRY(hs.init());
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2_nb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)InnerLayout<float, kM>::bytes));
+                                      (int)solve_smem(InnerLayout<float, kM>::bytes)));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
     PassMaps maps1[2], maps2[2];                         // per buffer set: pass 1, pass 2 and V
     for (int set = 0; set < 2; ++set) {
@@ -399,7 +399,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
             if (set < 0) return MPJ_CUDA_ERROR;
             {
                 MPJ_PROF(PC_SOLVE2_F32, s);
-                k_solve2_nb<<<K, kSolveThreads, InnerLayout<float, kM>::bytes, s>>>(
+                k_solve2_nb<<<K, kSolveThreads, solve_smem(InnerLayout<float, kM>::bytes), s>>>(
                     T, N, Wbuf[set], Sbuf[set], Fimg[set], fmax[set], r, (float)eps_skip, tau, gate, max_inner,
                     cross, rot);
             }

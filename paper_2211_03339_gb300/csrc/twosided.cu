@@ -103,7 +103,7 @@ template <class Real, int B>
 static int configure_twosided() {
     constexpr int M = 2 * B;
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2<Real, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)InnerLayout<Real, M>::bytes));
+                                      (int)solve_smem(InnerLayout<Real, M>::bytes)));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_apply2T<Real, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)ApplySmem<Real, B>::t));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_apply2V<Real, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -120,7 +120,7 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
     const int K = N / M;
     const bool dbl = sizeof(Real) == 8;
     { MPJ_PROF(dbl ? PC_SOLVE2_F64 : PC_SOLVE2_F32, s);
-      k_solve2<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(T, N, Wbuf, fmax, r, eps, tau,
+      k_solve2<Real, B><<<K, kSolveThreads, solve_smem(InnerLayout<Real, M>::bytes), s>>>(T, N, Wbuf, fmax, r, eps, tau,
                                                                          gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot,
                                                                          Fsplit); }
     MPJ_LAUNCH_CHECK("k_solve2");
