@@ -155,23 +155,61 @@ __device__ __forceinline__ void step_update_s(Real* S, const Real* cs, const int
 
 // F <- F J + (J - I) for the rotations of one step buffer (columns p, q of every
 // rotation), by the threads t0, t0 + nt, ... (t0 = this thread's index among them).
+// FP64: items [0, P (M - 2)) are the rows other than p and q of each rotation
+// (plain rotations of two entries); the last 2P items are rows p and q, which
+// also get the entries of J - I (c - 1 and +-s).  Keeping those few rows apart
+// spares the other lanes predicated FP64 corrections, which occupy the FP64
+// pipe like executed ones.  FP32 keeps one item per (row, rotation).
 template <class Real, int M>
 __device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int* ip, int t0, int nt) {
     constexpr int LD = M + 1;
     constexpr int P = M / 2;
+    constexpr int R = M - 2;
     const Real* sn = cs + P;
     const Real* cm = cs + 2 * P;
     const int* iq = ip + P;
     const int* sk = ip + 2 * P;
+    if constexpr (sizeof(Real) != 8) {
+        for (int t = t0; t < M * P; t += nt) {
+            int row = t % M, a = t / M;
+            if (sk[a]) continue;
+            int pa = ip[a], qa = iq[a];
+            Real c = cs[a], s = sn[a];
+            Real fp = F[pa * LD + row], fq = F[qa * LD + row];
+            Real np = c * fp - s * fq, nq = s * fp + c * fq;
+            if (row == pa) { np += cm[a]; nq += s; }
+            else if (row == qa) { np -= s; nq += cm[a]; }
+            F[pa * LD + row] = np;
+            F[qa * LD + row] = nq;
+        }
+        return;
+    }
     for (int t = t0; t < M * P; t += nt) {
-        int row = t % M, a = t / M;
+        int a, row;
+        const bool regular = t < P * R;
+        if (regular) {
+            a = t / R;
+            row = t - a * R;
+        } else {
+            a = (t - P * R) >> 1;
+            row = 0;
+        }
         if (sk[a]) continue;
-        int pa = ip[a], qa = iq[a];
-        Real c = cs[a], s = sn[a];
-        Real fp = F[pa * LD + row], fq = F[qa * LD + row];
+        const int pa = ip[a], qa = iq[a];                  // pa < qa
+        if (regular) {
+            row += row >= pa;
+            row += row >= qa;
+        } else {
+            row = (t & 1) ? qa : pa;
+        }
+        const Real c = cs[a], s = sn[a];
+        const Real fp = F[pa * LD + row], fq = F[qa * LD + row];
         Real np = c * fp - s * fq, nq = s * fp + c * fq;
-        if (row == pa) { np += cm[a]; nq += s; }
-        else if (row == qa) { np -= s; nq += cm[a]; }
+        if (!regular) {
+            const bool atq = (t & 1) != 0;
+            np += atq ? -s : cm[a];
+            nq += atq ? cm[a] : s;
+        }
         F[pa * LD + row] = np;
         F[qa * LD + row] = nq;
     }
