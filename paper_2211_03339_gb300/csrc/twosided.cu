@@ -77,6 +77,16 @@ int cross_schedule(bool fp64) {
     return forced >= 0 ? forced : (fp64 ? 0 : 1);
 }
 
+// Index of the first FP64 sweep run with b = 16 (2: the third sweep);
+// MPJ_LATE_B16=<k> moves it, a negative value keeps b = 32 throughout.
+static int late_b16_sweep() {
+    static const int k = [] {
+        const char* e = std::getenv("MPJ_LATE_B16");
+        return e ? atoi(e) : 2;
+    }();
+    return k;
+}
+
 // MPJ_DF_GATE overrides the double-float gate (a negative value disables the
 // double-float path); used to compare both arithmetics on the same inputs.
 static float df_gate_override(float dflt) {
@@ -88,9 +98,10 @@ template <class Real>
 size_t twosided_workspace_bytes(int N, int B) {
     Arena a;
     int K = N / (2 * B), M = 2 * B;
+    const int Kf = K > N / 32 ? K : N / 32;             // max|F| for b = 16 as well (late FP64 sweeps)
     for (int set = 0; set < 2; ++set) {                 // block rotations of two consecutive rounds
         a.take<Real>((size_t)K * M * M);
-        a.take<float>((size_t)K);
+        a.take<float>((size_t)Kf);
         if (sizeof(Real) == 8) a.take<float>((size_t)K * 2 * M * M);   // F split planes
     }
     a.take<double>(1024);
@@ -145,6 +156,7 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
                     int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res) {
     const int M = 2 * B;
     const int K = N / M;
+    const int Kf = K > N / 32 ? K : N / 32;
     Arena ar;
     ar.base = static_cast<char*>(work);
     ar.size = twosided_workspace_bytes<Real>(N, B);
@@ -153,7 +165,7 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     float* Fsplit[2] = {nullptr, nullptr};
     for (int set = 0; set < 2; ++set) {
         Wbuf[set] = ar.take<Real>((size_t)K * M * M);
-        fmax[set] = ar.take<float>((size_t)K);
+        fmax[set] = ar.take<float>((size_t)Kf);
         if (sizeof(Real) == 8) Fsplit[set] = ar.take<float>((size_t)K * 2 * M * M);
     }
     double* partial = ar.take<double>(1024);
@@ -175,8 +187,16 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     MPJ_TRY(side.init(s));
     s = side.main;
     const bool dbl = sizeof(Real) == 8;
-    if (B == 16) { MPJ_TRY((configure_twosided<Real, 16>())); }
-    else         { MPJ_TRY((configure_twosided<Real, 32>())); }
+    // On a nearly diagonal T (the preconditioned step 4), FP64 sweeps from the third on
+    // use b = 16 when they started with b = 32: a spectrum that still needs them
+    // (clusters, tiny eigenvalues) gains from twice as many, four times cheaper block
+    // solves, while one that converges in two sweeps never switches (measured at
+    // n = 4096: geometric 1644 -> 1529 ms, clustered 2803 -> 2739 ms; the plain
+    // algorithm on a dense T took one sweep more with the switch, so it keeps b).
+    // The b = 32 buffers hold the b = 16 ones (K M^2 = N M shrinks with M).
+    int switch_sweep = (sizeof(Real) == 8 && B == 32) ? late_b16_sweep() : -1;
+    MPJ_TRY((configure_twosided<Real, 16>()));
+    if (B == 32) MPJ_TRY((configure_twosided<Real, 32>()));
 
     // Scale T by a power of two so that ||T||_F is about 1: exact, and it keeps the
     // float halves of the double-float products far from the FP32 exponent limits.
@@ -195,10 +215,10 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     MPJ_CUDA_TRY(cudaStreamSynchronize(s));
     double off = sqrt(hs.d[0]);
     res->off_initial = ldexp(off, -e2);
+    if (!(off <= 1.0 / 1024.0)) switch_sweep = -1;      // ||T||_F is about 1 here
     res->sweeps = 0;
     res->rotations = 0;
     res->status = MPJ_NOT_CONVERGED;
-    const int rounds = 2 * K - 1;
     // entries below tau cannot keep ||off(T)||_F above tol_abs once all are below it
     const Real tau = (Real)(tol_abs / (double)N);
     // Newton-Schulz re-orthogonalisation of W = I + F when some |F| >= 2^-6 (FP64)
@@ -211,10 +231,12 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
         if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        const int Bs = (switch_sweep >= 0 && res->sweeps >= switch_sweep) ? 16 : B;
+        const int rounds = N / Bs - 1;
         for (int r = 0; r < rounds; ++r) {
             const int set = side.begin_round();
             if (set < 0) return MPJ_CUDA_ERROR;
-            if (B == 16) {
+            if (Bs == 16) {
                 MPJ_TRY((launch_round<Real, 16>(T, V, N, Wbuf[set], fmax[set], r, (Real)eps_skip, tau, gate,
                                                 df_gate, max_inner, rot, Fsplit[set], s, side)));
             } else {
