@@ -277,6 +277,21 @@ def test_syevj_multiple_eigenvalues(mpj, mode):
         assert np.abs(L - lam).max() <= 14 * n * U * np.abs(lam).max()
 
 
+def test_syevj_mp_geometric_late_b16(mpj):
+    """Geometric spectrum at n = 1024: after preconditioning T is nearly diagonal but
+    needs more than two FP64 sweeps, so the sweeps from the third on run with b = 16.
+    Residual, orthogonality and the constructed eigenvalues within the bounds."""
+    n = 1024
+    A, lam = synth.sym_matrix(n, "geometric", seed=synth.seed_for(1, 77))
+    L, V, st = mpj.syevj_mp(dev(A))
+    L, V = host(L), host(V)
+    assert st["sweeps"] > 2, st
+    res, orth = evd_metrics(A, L, V)
+    assert res <= 10 * n * U and orth <= 10 * n * U, (res, orth)
+    a2 = np.abs(lam).max()
+    assert np.abs(L - lam).max() <= 10 * n * U * a2 + 4 * n * U * a2
+
+
 def test_syevj_mp_n8192_properties(mpj):
     """Largest single-matrix size of the workload (n = 8192), preconditioned path."""
     n = 8192

@@ -81,3 +81,25 @@ def test_synth_batch_sizes_range_and_seed():
     a = synth.batch_sizes(10000, 8, 256, seed=3000)
     b = synth.batch_sizes(10000, 8, 256, seed=3000)
     assert np.array_equal(a, b) and a.min() >= 8 and a.max() <= 256
+
+
+@pytest.mark.parametrize("n", [512, 1024, 1280, 4096])
+def test_alg_counts_closed_forms(n):
+    """bench.alg_counts follows the library's schedule; its totals must equal the
+    method's own counts: MGS 2 n^3 (column MGS inside 32-column panels, their
+    projections and updates, and for n >= 1024 the exactly split projections
+    between 256-column panels), the congruence 2 n^3 + n^2 (n + 1) on the tensor
+    cores (A Q in full, Q^T W on the upper triangle), and 3 n^3 per FP64 sweep for T."""
+    import bench
+    c, realised = bench.alg_counts(n, 2, 11)
+    oz_fp64 = c["oz_gemm"] / 36.0
+    congruence = 2.0 * n ** 3 + n * n * (n + 1)
+    mgs_fp64 = c["mgs_panel"] + c["mgs_proj"] + c["dgemm_f64"] + (oz_fp64 - congruence)
+    assert mgs_fp64 == pytest.approx(2.0 * n ** 3, rel=1e-12)
+    if n < 1024:
+        assert oz_fp64 == pytest.approx(congruence, rel=1e-12)
+    assert c["apply2_f64"] == 2 * 3.0 * n ** 3
+    Np = -(-n // 64) * 64
+    assert realised["apply2_f64"] == 2 * 4.0 * Np ** 3
+    # one FP32 matrix read and written per pass and round
+    assert c["tc1_f32"] == 8.0 * Np * Np * (Np // 32 - 1) * 11
