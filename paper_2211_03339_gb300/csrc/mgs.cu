@@ -3,13 +3,16 @@
 // The columns are processed in panels of 32.  A panel is orthogonalised by
 // classic column-by-column MGS:
 //     r_jj = ||w_j||,  q_j = w_j / r_jj,  w_k = w_k - (q_j^T w_k) q_j  (k > j in panel)
-// by ONE thread-block cluster of 8 CTAs that splits the m rows between its
-// CTAs.  For each column the CTAs form partial inner products w_j^T w_k over
-// their rows, exchange them through distributed shared memory (one cluster
-// barrier per column, double-buffered), sum them in a fixed order, and update
-// their rows.  Rows are read with consecutive threads on consecutive rows
-// (coalesced, column-major).  The trailing columns then receive the panel's
-// projections, W = W - Q_p (Q_p^T W), as two FP64 GEMMs (block MGS).
+// by ONE thread-block cluster (16 CTAs where the device runs clusters that
+// large, else 8) that splits the m rows between its CTAs; each CTA keeps its
+// rows of the panel in shared memory (k_mgs_panel_smem; k_mgs_panel reads them
+// from global memory when they do not fit).  For each column the CTAs form
+// partial inner products w_j^T w_k over their rows, exchange them through
+// distributed shared memory (one cluster barrier per column, double-buffered),
+// sum them in a fixed order, and update their rows.  The trailing columns then
+// receive the panel's projections, W = W - Q_p (Q_p^T W), as two FP64 GEMMs
+// (block MGS); for n >= 1024 the columns are first grouped in 256-column panels
+// whose projections run on the tensor cores (mgs_blocked_oz).
 #include <cooperative_groups.h>
 #include <cmath>
 #include <cstdlib>

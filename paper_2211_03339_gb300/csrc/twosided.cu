@@ -13,7 +13,10 @@
 //             W_a^T T[IJ_a, IJ_b] W_b (and its transpose is mirrored), and every
 //             64-row slab of V becomes V[:, IJ_b] W_b.
 // ||off(T)||_F is reduced once per sweep and read back for the while-test.
-// k_apply2 is two kernels: k_apply2T (tiles of T) and k_apply2V (slabs of V).
+// k_apply2 is two kernels: k_apply2T (tiles of T) and k_apply2V (slabs of V);
+// k_apply2V runs on a low-priority second stream, overlapping the next round's
+// block solves (the rotations of two rounds are double buffered).  FP64 sweeps
+// of a nearly diagonal T switch from b = 32 to b = 16 from the third sweep on.
 #include <cmath>
 #include <cstdio>
 
