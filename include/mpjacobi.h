@@ -194,13 +194,18 @@ int mpj_stage1_syevj32(const double* A, int n, int lda, double* Z, int ldz, doub
 /* Lemma 2.1 / step 2 of Alg. 4.1: modified Gram-Schmidt Z = Q R (m x n, m >= n) in
  * FP64, blocked: each 32-column panel is orthogonalised column by column (MGS)
  * by one thread-block cluster, then the trailing columns are projected against
- * the panel (two FP64 GEMMs).  R is not formed.  Returns MPJ_RANK_DEFICIENT if
- * some r_jj == 0. */
+ * the panel (two FP64 GEMMs).  For n >= 1024 the columns are first grouped in
+ * 256-column panels, orthogonalised in order; the projections between those
+ * panels are FP64 products on the tensor cores by exact splitting (error of the
+ * order of an FP64 dot product's rounding).  R is not formed.  Returns
+ * MPJ_RANK_DEFICIENT if some r_jj == 0. */
 int mpj_mgs(const double* Z, int m, int n, int ldz, double* Q, int ldq,
             void* work, size_t work_bytes, void* stream);
 size_t mpj_mgs_workspace_bytes(int m, int n);
 
-/* mpj_mgs_noalloc -- the same blocked MGS as mpj_mgs for callers that cannot
+/* mpj_mgs_noalloc -- the blocked MGS of mpj_mgs, with 32-column panels at every
+ * size (the tensor-core projections between 256-column panels need scratch of
+ * their own), for callers that cannot
  * allocate device memory at call time: for instance code running where an
  * allocation could block on a device-wide synchronisation or fail under memory
  * pressure (a latency-critical loop), or applications whose own memory manager
@@ -224,7 +229,11 @@ size_t mpj_mgs_workspace_bytes(int m, int n);
 int mpj_mgs_noalloc(const double* Z, int m, int n, int ldz, double* Q, int ldq, void* stream);
 
 /* Step 3 of Alg. 4.1: T = Q^T (A Q) in FP64 (A n x n symmetric, Q n x n).  The
- * upper triangle is computed and mirrored, so T is exactly symmetric. */
+ * upper triangle is computed and mirrored, so T is exactly symmetric.  Both
+ * products run on the bf16 tensor cores by exact splitting (8 slices of 7 bits
+ * per row of op(A) / column of op(B), power-of-two scaled); the error stays
+ * within the bound of an FP64 product, |T - Q^T A Q| <= 2 gamma_n (2 + gamma_n)
+ * |Q|^T |A| |Q| elementwise (Sec. 4).  n > 32768 uses FP64 GEMMs. */
 int mpj_congruence(const double* A, int lda, const double* Q, int ldq, int n,
                    double* T, int ldt, void* work, size_t work_bytes, void* stream);
 size_t mpj_congruence_workspace_bytes(int n);
