@@ -112,6 +112,7 @@ inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 int choose_block(int n, const mpj_options* o);
 int fp64_block(int B);
 size_t solve_smem(size_t need);
+bool v_after_t(bool tc32);
 
 // ---------------------------------------------------------------- engines
 // Two-sided block Jacobi (Alg. 3.2 / step 4 of Alg. 4.1, parallel round-robin

@@ -123,6 +123,17 @@ size_t solve_smem(size_t need) {
     return excl && need < x ? x : need;
 }
 
+// Where the V stream joins a round: after the block solves, or after the T
+// update, so that the V update overlaps only the next round's solves and not
+// the T passes.  MPJ_V_AFTER_T is a bit mask: bit 1 the tensor-core FP32 stage,
+// bit 2 the two-sided engine.  Default 1: measured at n = 4096, the FP32 stage's
+// V pass after pass 2 saves 14 ms (pass 2 no longer shares the SMs with it),
+// while the FP64 V update after the tile update costs 5 ms.
+bool v_after_t(bool tc32) {
+    static const int mask = [] { const char* e = std::getenv("MPJ_V_AFTER_T"); return e ? atoi(e) : 1; }();
+    return (mask & (tc32 ? 1 : 2)) != 0;
+}
+
 // Block size of the FP64 sweeps of the EVD: the stage-1 size B unless
 // MPJ_B64=16 asks for b = 16 there (N stays a multiple of 2B, so of 32).
 int fp64_block(int B) {

@@ -390,6 +390,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     const float tau = (float)(tol_abs / (double)N);
     const float gate = 1.0f / 4096.0f;                   // Newton-Schulz when some |F| >= 2^-12
     const int cross = N >= kB * kB ? cross_schedule(false) : 0;     // see cross_schedule
+    const bool v_late = v_after_t(true);
     while (res->sweeps < max_sweeps) {
         if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
@@ -404,7 +405,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
                     cross, rot);
             }
             MPJ_LAUNCH_CHECK("k_solve2_nb");
-            MPJ_TRY(side.after_solve());
+            if (!v_late) MPJ_TRY(side.after_solve());
             {
                 MPJ_PROF(PC_TC1_F32, s);
                 k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps1[set], P, N, n_slabs, items, items, nullptr,
@@ -417,6 +418,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
                                                                fmax[set], r, rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc pass 2");
+            if (v_late) MPJ_TRY(side.after_solve());
             {
                 // Persistent (two CTAs per SM) while a CTA has few tiles; one tile per CTA
                 // for N >= 8192, where the SM slots then free up tile by tile for the next

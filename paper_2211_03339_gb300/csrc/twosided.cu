@@ -138,13 +138,15 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
                                                                          gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot,
                                                                          Fsplit); }
     MPJ_LAUNCH_CHECK("k_solve2");
-    MPJ_TRY(side.after_solve());
+    const bool v_late = v_after_t(false);
+    if (!v_late) MPJ_TRY(side.after_solve());
     int n_ttiles = K * (K - 1) / 2;
     if (n_ttiles > 0) {
         MPJ_PROF(dbl ? PC_APPLY2_F64 : PC_APPLY2_F32, s);
         k_apply2T<Real, B><<<n_ttiles, kThreads, ApplySmem<Real, B>::t, s>>>(T, N, Wbuf, fmax, r, df_gate, Fsplit);
         MPJ_LAUNCH_CHECK("k_apply2T");
     }
+    if (v_late) MPJ_TRY(side.after_solve());
     {
         MPJ_PROF(dbl ? PC_APPLY2V_F64 : PC_APPLY2V_F32, sv);
         k_apply2V<Real, B><<<(N / M) * K, kThreads, ApplySmem<Real, B>::v, sv>>>(V, N, Wbuf, fmax, r, df_gate, Fsplit);
