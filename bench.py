@@ -451,7 +451,7 @@ def run_ours(args):
     fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
     df_peak = 152 * 128 / 11 * 2 * 2.070e9 / 1e12     # 11 FP32 instructions per double-float MAC
     hbm_peak, hbm_note = measured_hbm()
-    fp64 = (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (nominal; DESIGN.md has the probe rates)", "alu", "TFLOP/s")
+    fp64 = (FP64_PEAK_TFLOPS, "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (nominal; probe on this GB300: 1.02 TFLOP/s DFMA, 1.06 DMMA)", "alu", "TFLOP/s")
     dfp = (df_peak, "double-float on FP32: 152 x 128 lanes / 11 instr per MAC x 2 x 2.07 GHz", "alu", "TFLOP/s")
     f32p = (fp32_peak, "FP32 FFMA: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz", "alu", "TFLOP/s")
     hbm = (hbm_peak, hbm_note, "hbm", "GB/s")
