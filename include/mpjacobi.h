@@ -205,21 +205,25 @@ size_t mpj_mgs_workspace_bytes(int m, int n);
 
 /* mpj_mgs_noalloc -- the blocked MGS of mpj_mgs, with 32-column panels at every
  * size (the tensor-core projections between 256-column panels need scratch of
- * their own), for callers that cannot
- * allocate device memory at call time: for instance code running where an
- * allocation could block on a device-wide synchronisation or fail under memory
- * pressure (a latency-critical loop), or applications whose own memory manager
- * owns all device memory and does not allow allocations from libraries.  The
- * paper has no counterpart: this is a service variant of Lemma 2.1's step.
+ * their own), for callers that cannot allocate device memory at call time:
+ * for instance code running where an allocation could block on a device-wide
+ * synchronisation or fail under memory pressure (a latency-critical loop), or
+ * applications whose own memory manager owns all device memory and does not
+ * allow allocations from libraries.  The paper has no counterpart.
  *   Z, m, n, ldz, Q, ldq, stream: as for mpj_mgs.  Nothing is allocated and
  *   nothing is freed (no cudaMalloc, cudaFree or allocating library routine).
  *   Scratch: a fixed device array of MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES
- *   doubles (8 MiB) compiled into the library; it is reserved on every GPU that
- *   loads the library until the process exits.  A call needs
- *   32 * n * (1 + ceil(m / 256)) doubles of it (square Z: up to n = 2048);
- *   larger sizes are rejected with MPJ_BAD_ARG before any device work.
- *   The first call on a device looks up the array's device address (a host-side
- *   set-up step); make that first call before any stream capture.
+ *   doubles (8 MiB) compiled into the library.  A call needs
+ *   32 * n * (1 + ceil(m / 256)) doubles of it (a square Z fits up to
+ *   n = 2730); larger sizes are rejected with MPJ_BAD_ARG before any device
+ *   work.
+ *   The array is reserved on a GPU when the library's module is loaded there,
+ *   which with CUDA's lazy module loading happens at the first call of the
+ *   library on that GPU, and stays reserved until the process exits.  Make a
+ *   first call (of this or any other entry point) in set-up code, before any
+ *   stream capture, so that the reservation cannot fail later for lack of
+ *   memory.  Each call looks up the array's address in the CUDA context that
+ *   is current (a host-side query that allocates nothing).
  *   All calls share the one array, which keeps the previous call's contents:
  *   calls that may overlap on the GPU (different streams, or several host
  *   threads) race on it and must be serialised by the caller.

@@ -93,7 +93,7 @@ enum ProfClass {
     PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
     PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2_F32,
-    PC_OZ_SLICE, PC_OZ_GEMM, PC_TCV_F32, kProfClasses
+    PC_OZ_SLICE, PC_OZ_GEMM, PC_TCV_F32, PC_TCP1_F64, PC_TCP2_F64, PC_TCV_F64, kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -138,6 +138,14 @@ size_t tc32_workspace_bytes(int N);
 int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol_abs,
                          double eps_skip, int max_sweeps, int max_inner, void* work, cudaStream_t s,
                          SweepResult* res);
+// The FP64 engine with the rotations applied on the tensor cores by exact
+// splitting (tc64_apply.cu): block size b = 32, T and V column-major N x N.
+// The workspace holds the block rotations, their digit planes and the N x N
+// scratch P of pass 1.  cross selects the cross-pair inner schedule.
+size_t tc64_workspace_bytes(int N);
+bool tc64_supported(int N, int B);
+int twosided_sweeps_tc64(double* T, double* V, int N, int n, double tol_abs, double eps_skip, int max_sweeps,
+                         int max_inner, int cross, void* work, cudaStream_t s, SweepResult* res);
 // Z[:, c] = V[:, perm[c]] (widened) from a row-major V.
 int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double* Z, int ldz,
                         cudaStream_t s);

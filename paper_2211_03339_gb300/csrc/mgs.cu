@@ -368,30 +368,22 @@ int mgs_blocked_oz(double* Q, int m, int n, int ldq, void* work, int* d_flag, vo
 // mpj_mgs_noalloc runs the same blocked MGS as mpj_mgs but takes its scratch
 // (the panel projections R and their split partials, plus the rank flag) from
 // a fixed array compiled into the library instead of allocating it.  The array
-// lives in device global memory on every GPU that loads the library, from load
-// until the process exits.  In host code g_mgs_noalloc_scratch is only a
-// host-side stand-in for the device array, so its device address is looked up
-// with cudaGetSymbolAddress (once per device) and passed to the kernels.
+// lives in device global memory on every GPU where the library's module is
+// loaded, from the first call there until the process exits.  In host code
+// g_mgs_noalloc_scratch is only a host-side stand-in for the device array, so
+// its device address is looked up with cudaGetSymbolAddress and passed to the
+// kernels.  The address belongs to the CUDA context that is current, not to
+// the device ordinal, so it is looked up again on every call (a cheap query
+// once the module is loaded; it allocates nothing): a cached address would be
+// stale after cudaDeviceReset or under another context on the same device.
 static __device__ __align__(256) double g_mgs_noalloc_scratch[MPJ_MGS_NOALLOC_MAX_SCRATCH_DOUBLES + 32];
 
 namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device; the first call on
-// a device performs the lookup.
+// Device address of the scratch array in the current context.
 int noalloc_scratch(double** out) {
-    int dev = -1;
-    MPJ_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) { set_error_msg("device ordinal out of range"); return MPJ_BAD_ARG; }
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        MPJ_CUDA_TRY(cudaGetSymbolAddress(&p, g_mgs_noalloc_scratch));
-        g_noalloc_ptr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    MPJ_CUDA_TRY(cudaGetSymbolAddress(&p, g_mgs_noalloc_scratch));
+    *out = static_cast<double*>(p);
     return MPJ_SUCCESS;
 }
 }  // namespace

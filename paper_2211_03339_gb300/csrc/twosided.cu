@@ -110,7 +110,12 @@ size_t twosided_workspace_bytes(int N, int B) {
     a.take<double>(1024);
     a.take<double>(4);
     a.take<unsigned long long>(4);
-    return a.used + 256;
+    size_t bytes = a.used + 256;
+    if (sizeof(Real) == 8 && tc64_supported(N, B)) {
+        const size_t t = tc64_workspace_bytes(N);
+        bytes = t > bytes ? t : bytes;
+    }
+    return bytes;
 }
 
 template <class Real, int B>
@@ -159,6 +164,12 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
 template <class Real>
 int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, double eps_skip,
                     int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res) {
+    if constexpr (sizeof(Real) == 8) {
+        // b = 32: the block rotations are applied on the tensor cores (tc64_apply.cu)
+        if (tc_enabled() && tc64_supported(N, B))
+            return twosided_sweeps_tc64(T, V, N, n, tol_abs, eps_skip, max_sweeps, max_inner,
+                                        cross_schedule(true), work, s, res);
+    }
     const int M = 2 * B;
     const int K = N / M;
     const int Kf = K > N / 32 ? K : N / 32;

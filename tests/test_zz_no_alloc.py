@@ -34,7 +34,7 @@ def _col(Z):
     return torch.from_numpy(np.ascontiguousarray(np.asarray(Z).T)).cuda()
 
 
-def _call(fn_name, mpj, Z):
+def _call(fn_name, mpj, Z, expect=0):
     m, n = Z.shape
     L = mpj.lib()
     Zd = _col(Z)
@@ -47,7 +47,7 @@ def _call(fn_name, mpj, Z):
     else:
         rc = L.mpj_mgs_noalloc(ctypes.c_void_p(Zd.data_ptr()), m, n, m,
                                ctypes.c_void_p(Qd.data_ptr()), m, stream)
-    assert rc == 0, (fn_name, rc)
+    assert rc == expect, (fn_name, rc)
     return Qd.cpu().numpy().T
 
 
@@ -65,6 +65,22 @@ def test_mgs_noalloc_matches_mgs_on_two_calls(mpj):
         Q_new = _call("mpj_mgs_noalloc", mpj, Z)
         assert np.abs(Q_new - Q_ref).max() <= 10 * n * U * kappa
         assert np.linalg.norm(Q_new.T @ Q_new - np.eye(n)) <= 10 * n * U * kappa
+
+
+def test_mgs_noalloc_clears_the_rank_flag_between_calls(mpj):
+    """The rank flag lives in the shared array: a call on a Z with a zero column
+    reports MPJ_RANK_DEFICIENT (4), and the next call on a full-rank Z must start
+    from a cleared flag, return 0 and match mpj_mgs."""
+    rng = np.random.default_rng(7303)
+    Zbad = rng.standard_normal((200, 96))
+    Zbad[:, 40] = 0.0
+    _call("mpj_mgs_noalloc", mpj, Zbad, expect=4)
+    Z = rng.standard_normal((200, 96))
+    n = Z.shape[1]
+    kappa = np.linalg.cond(Z)
+    Q_new = _call("mpj_mgs_noalloc", mpj, Z)
+    Q_ref = _call("mpj_mgs", mpj, Z)
+    assert np.abs(Q_new - Q_ref).max() <= 10 * n * U * kappa
 
 
 def test_mgs_noalloc_rejects_sizes_beyond_its_scratch(mpj):
