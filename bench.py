@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads (spectra, orders 1024-8192, SVD shapes)")
     ap.add_argument("--batch", type=int, default=10000, help="matrices in the batched workload")
     ap.add_argument("--once", action="store_true",
                     help="run one mpj_syevj_mp solve and exit (for profiler captures)")
@@ -176,22 +178,57 @@ def dist_setup(args):
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(spectrum, seed, n_sample=512):
-    """Alg. 4.1 in the CPU oracle at n_sample; returns (seconds, stats)."""
+ORACLE_N = 384          # order of the oracle's sample solves (a few seconds each on one core)
+
+
+def _oracle_solve(job):
+    """One full oracle Alg. 4.1 solve (its own process); returns (seconds, sweeps, stage-1 sweeps)."""
+    spectrum, seed, n = job
     import oracle
     from paper_2211_03339_gb300 import synth
-    A, _ = synth.sym_matrix(n_sample, spectrum, seed=seed)
+    A, _ = synth.sym_matrix(n, spectrum, seed=seed)
     t = time.perf_counter()
     L, V, st, rc = oracle.syevj_mp(A)
-    return time.perf_counter() - t, st
+    return time.perf_counter() - t, st["sweeps"], st["sweeps_stage1"]
 
 
-def cpu_baseline(args, n_sample=512):
-    sec, st = oracle_sample(args.spectrum, synth_seed(0), n_sample)
-    scale = (args.n / n_sample) ** 3
-    return {"value": 1.0 / (sec * scale), "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle Alg. 4.1 (scalar C, 1 thread) on one n={n_sample} {args.spectrum} "
-                      f"matrix: {sec:.2f} s, scaled by (n/{n_sample})^3 = {scale:.0f} to n={args.n}"}
+class OraclePool:
+    """One process per host core ("spawn": started before any GPU work of this
+    process), each running the unmodified CPU oracle on its own matrix."""
+
+    def __init__(self, procs=None):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.procs = procs or (os.cpu_count() or 1)
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+
+    def step(self, spectrum, step_index, n_target):
+        """Solve `procs` independent n = ORACLE_N matrices at once; returns the wall
+        time, the rate scaled to n_target solves/s and the sweep counts."""
+        jobs = [(spectrum, synth_seed(100 * step_index + i), ORACLE_N) for i in range(self.procs)]
+        t = time.perf_counter()
+        out = self.pool.map(_oracle_solve, jobs)
+        wall = time.perf_counter() - t
+        scale = (ORACLE_N / n_target) ** 3
+        return wall, self.procs * scale / wall, [o[1] for o in out], [o[2] for o in out]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def describe(self, spectrum, wall, sw, sw1, n_target):
+        return (f"{self.procs} concurrent full runs of the unmodified oracle Alg. 4.1 (scalar C, one process "
+                f"per host core) on n={ORACLE_N} {spectrum} matrices of the same recipe: {wall:.2f} s wall, "
+                f"FP64 sweeps {min(sw)}-{max(sw)}, FP32 sweeps {min(sw1)}-{max(sw1)}; the rate is scaled to "
+                f"n={n_target} solves by the method's n^3 work, ({ORACLE_N}/{n_target})^3, which assumes the "
+                f"sweep counts of n={ORACLE_N}")
+
+
+def cpu_baseline(args, pool):
+    wall, rate, sw, sw1 = pool.step(args.spectrum, 0, args.n)
+    return {"value": rate, "unit": "solves/s", "cores": pool.procs, "kind": "oracle",
+            "sample": pool.describe(args.spectrum, wall, sw, sw1, args.n)}
 
 
 def synth_seed(index):
@@ -203,24 +240,27 @@ def run_reference(args):
     world, rank, local, pg = dist_setup(args)
     if rank != 0:
         return 0
-    n_sample = 512
-    for _ in range(args.warmup):
-        oracle_sample(args.spectrum, synth_seed(0), n_sample)
-    times = []
+    pool = OraclePool()
+    for w in range(args.warmup):
+        pool.step(args.spectrum, w, args.n)
+    walls, sws, sw1s = [], [], []
     for k in range(args.steps):
-        sec, st = oracle_sample(args.spectrum, synth_seed(0), n_sample)
-        times.append(sec * (args.n / n_sample) ** 3)
-    tot = sum(times)
-    value = args.steps / tot
+        wall, rate, sw, sw1 = pool.step(args.spectrum, args.warmup + k, args.n)
+        walls.append(wall); sws += sw; sw1s += sw1
+    pool.close()
+    tot = sum(walls)
+    value = args.steps * pool.procs * (ORACLE_N / args.n) ** 3 / tot
+    desc = pool.describe(args.spectrum, tot / args.steps, sws, sw1s, args.n)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"syevj_mp n={args.n} {args.spectrum} spectrum (oracle sample n={n_sample})",
-                       "n": args.n, "spectrum": args.spectrum},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: oracle Alg. 4.1 at n={n_sample}, time scaled by "
-                                       f"(n/{n_sample})^3"},
+            "config": {"workload": f"CPU oracle Alg. 4.1: each step {pool.procs} concurrent solves of n={ORACLE_N} "
+                                   f"{args.spectrum} matrices (a bounded sample of the n={args.n} workload; "
+                                   f"rate scaled by the n^3 work)",
+                       "n": args.n, "n_sample": ORACLE_N, "spectrum": args.spectrum},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": pool.procs, "kind": "oracle",
+                             "sample": "each step: " + desc},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -239,6 +279,72 @@ def accuracy(A, lam_true, L, V):
     err = float((L - lam_true).abs().max())
     return {"res_over_nu": res / (n * U), "orth_over_nu": orth / (n * U),
             "lamerr_over_nu_a2": err / (n * U * a2)}
+
+
+def run_extras(args, dev):
+    """The other single-matrix workloads of the benchmark configurations, one timed
+    call each after a warm-up call (CUDA events around the call on its stream):
+    Alg. 4.1 against Alg. 3.2 for the geometric and clustered spectra at n = 4096
+    and the uniform spectrum at n = 1024, 2048 and 8192, and Alg. 5.2 against Alg.
+    5.1 for the SVD shapes 4096 x 2048 and 8192 x 1024 (sigma geometric from 1 to
+    1e-10).  Accuracy in units of n u: residual, orthogonality, and the eigenvalue
+    (singular value) error against the constructed spectrum in units of n u ||A||_2
+    (sigma_1)."""
+    import numpy as np
+    import torch
+    import paper_2211_03339_gb300 as mpj
+    from paper_2211_03339_gb300 import synth
+    out = {}
+
+    def timed(fn, *a, **kw):
+        stream = torch.cuda.current_stream(dev)
+        fn(*a, **kw)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = fn(*a, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), r
+
+    for kind, n in (("geometric", 4096), ("cluster", 4096), ("uniform", 1024), ("uniform", 2048),
+                    ("uniform", 8192)):
+        A_np, lam = synth.sym_matrix(n, kind, seed=synth.seed_for(1, n))
+        A = torch.from_numpy(A_np).to(dev)
+        lam_t = torch.from_numpy(lam).to(dev)
+        entry = {}
+        for name, fn in (("mp", mpj.syevj_mp), ("plain", mpj.syevj_plain)):
+            ms, (L, V, st) = timed(fn, A, options={"max_sweeps": 60})
+            acc = accuracy(A, lam_t, L, V)
+            entry[name] = {"ms": ms, "sweeps": st["sweeps"], "sweeps_stage1": st["sweeps_stage1"],
+                           "stages_ms": st["ms_stage"], **acc}
+            del L, V
+        entry["speedup_mp_over_plain"] = entry["plain"]["ms"] / entry["mp"]["ms"]
+        out[f"syevj_{kind}_n{n}"] = entry
+        del A
+        torch.cuda.empty_cache()
+    for m, n, idx in ((4096, 2048, 0), (8192, 1024, 1)):
+        A_np, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, idx), sigma_min=1e-10)
+        A = torch.from_numpy(A_np).to(dev)
+        entry = {}
+        for name, fn in (("mp", mpj.gesvj_mp), ("plain", mpj.gesvj_plain)):
+            ms, (S, Uo, V, st) = timed(fn, A, options={"max_sweeps": 80})
+            I = torch.eye(n, dtype=torch.float64, device=dev)
+            res = (torch.linalg.matrix_norm(A @ V - Uo * S[None, :]) / torch.linalg.matrix_norm(A)).item()
+            oru = torch.linalg.matrix_norm(Uo.T @ Uo - I).item()
+            orv = torch.linalg.matrix_norm(V.T @ V - I).item()
+            Sn = S.cpu().numpy()
+            entry[name] = {"ms": ms, "sweeps": st["sweeps"], "sweeps_stage1": st["sweeps_stage1"],
+                           "JU_over_N": st["rotations"], "stages_ms": st["ms_stage"],
+                           "res_over_nu": res / (n * U), "orthU_over_nu": oru / (n * U),
+                           "orthV_over_nu": orv / (n * U),
+                           "sigma_err_over_nu_s1": float(np.max(np.abs(Sn - sig))) / (n * U * sig[0])}
+            del S, Uo, V
+        entry["speedup_mp_over_plain"] = entry["plain"]["ms"] / entry["mp"]["ms"]
+        out[f"gesvj_{m}x{n}"] = entry
+        del A
+        torch.cuda.empty_cache()
+    return out
 
 
 def run_batched(args, dev, world):
@@ -332,9 +438,11 @@ def run_backward(args, dev):
 
 def run_ours(args):
     import numpy as np
-    import torch
 
     world, rank, local, pg = dist_setup(args)
+    # the oracle's worker processes are started before this process touches the GPU
+    pool = OraclePool() if (rank == 0 and not args.no_cpu_baseline) else None
+    import torch
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     import __graft_entry__
@@ -438,6 +546,8 @@ def run_ours(args):
         batched = run_batched(args, dev, world)
     backward = None if args.no_batched else run_backward(args, dev)
 
+    extras = None if args.no_extras else run_extras(args, dev)
+
     if rank != 0:
         return 0
 
@@ -447,7 +557,7 @@ def run_ours(args):
     # next block solves; their event times include that overlap, so their shares
     # do not add up with the others and they are not candidates for "dominant".
     counts, realised = alg_counts(n, stats["sweeps"], stats["sweeps_stage1"])
-    side_classes = {"apply2v_f64", "apply2v_f32", "tcv_f32"}
+    side_classes = {"apply2v_f64", "apply2v_f32", "tcv_f32", "tcv_f64"}
     fp32_peak = 152 * 128 * 2 * 2.070e9 / 1e12
     df_peak = 152 * 128 / 11 * 2 * 2.070e9 / 1e12     # 11 FP32 instructions per double-float MAC
     hbm_peak, hbm_note = measured_hbm()
@@ -461,7 +571,7 @@ def run_ours(args):
     peaks = {"dgemm_f64": fp64, "mgs_proj": fp64, "mgs_panel": fp64, "solve2_f64": fp64,
              "apply2_f64": dfp, "apply2v_f64": dfp, "solve2_f32": f32p,
              "apply2_f32": f32p, "apply2v_f32": f32p, "tc1_f32": hbm, "tc2_f32": hbm, "tcv_f32": hbm,
-             "oz_gemm": tensor, "oz_slice": hbm}
+             "oz_gemm": tensor, "oz_slice": hbm, "tcp1_f64": hbm, "tcp2_f64": hbm, "tcv_f64": hbm}
     rooflines = {}
     for name, (nl, ms) in prof.items():
         if name not in counts or nl == 0 or counts[name] <= 0:
@@ -486,8 +596,9 @@ def run_ours(args):
     roof = rooflines[dname]
 
     cpu = None
-    if not args.no_cpu_baseline:
-        cpu = cpu_baseline(args)
+    if pool is not None:
+        cpu = cpu_baseline(args, pool)
+        pool.close()
 
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
@@ -511,6 +622,7 @@ def run_ours(args):
         "sweeps_stage1": stats["sweeps_stage1"], "off_T0": stats["off_T0"],
         "accuracy_mp": acc_mp, "plain": plain, "batched": batched,
         "backward": backward,
+        "configs": extras,
         "kernels_ms": {k: round(v[1], 3) for k, v in prof.items() if v[0]},
     }
     print(json.dumps(line), flush=True)
@@ -559,7 +671,9 @@ def alg_counts(n, sw64, sw32):
         panel32(n)
     sl(n, n); sl(n, n); oz(n, n, n)       # W = A Q
     sl(n, n); oz(n, n, n, upper=True)     # T = Q^T W (upper triangle, mirrored)
-    steps64 = M - 1                       # inner steps of an FP64 block solve
+    # inner steps of an FP64 block solve: the cross-pair schedule of the tensor-core
+    # FP64 engine (b = 32, N >= b^2), else the full tournament
+    steps64 = b + 1 if (b == 32 and Np >= b * b) else M - 1
     steps32 = b + 1 if Np >= b * b else M - 1   # cross schedule of the FP32 solves
     c["solve2_f64"] = sw64 * rounds * K * steps64 * 6.0 * M * M
     c["solve2_f32"] = sw32 * rounds * K * steps32 * 6.0 * M * M
@@ -568,6 +682,10 @@ def alg_counts(n, sw64, sw32):
     c["tc1_f32"] = 8.0 * Np * Np * rounds * sw32          # pass 1 reads T, writes P (FP32)
     c["tc2_f32"] = 8.0 * Np * Np * rounds * sw32          # pass 2 reads P, writes T
     c["tcv_f32"] = 8.0 * Np * Np * rounds * sw32          # V pass reads and writes V
+    if b == 32:                                            # tensor-core FP64 sweeps: FP64 in and out
+        c["tcp1_f64"] = 16.0 * Np * Np * rounds * sw64    # pass 1 reads T, writes P^T
+        c["tcp2_f64"] = 16.0 * Np * Np * rounds * sw64    # pass 2 reads P^T, writes T
+        c["tcv_f64"] = 16.0 * Np * Np * rounds * sw64     # V pass reads and writes V
     realised = {"apply2_f64": 4.0 * Np ** 3 * sw64, "apply2v_f64": 4.0 * Np ** 3 * sw64}
     return dict(c), realised
 

@@ -60,7 +60,10 @@ typedef struct mpj_stats {
     int    status;             /* same as the return value                        */
 } mpj_stats;
 
-/* Optional tuning knobs; pass NULL for the defaults. */
+/* Optional tuning knobs; pass NULL for the defaults (zero fields also mean
+ * "default").  The library reads no environment variables: every switch of its
+ * numerical path is a field of this struct, in effect for the one call that
+ * receives it. */
 typedef struct mpj_options {
     int    max_sweeps;         /* FP64 sweeps cap (default 40)                     */
     int    max_sweeps_stage1;  /* FP32 sweeps cap (default 40)                     */
@@ -70,7 +73,26 @@ typedef struct mpj_options {
     double ju_ratio;           /* one-sided stop: sweep applies < ju_ratio*N rotations
                                   (default 2e-4, Sec. 6)                           */
     int    block;              /* block size b: 16 or 32 (0 = choose by n)         */
+    int    flags;              /* MPJ_OPT_* bits: alternative paths for comparisons
+                                  and studies (0 = the default path)               */
+    int    stage1_tf32_terms;  /* TF32 products per rotation tile of the FP32 stage
+                                  (b = 32): 3 = hi*hi + hi*lo + lo*hi (default,
+                                  about FP32 accuracy), 1 = hi*hi only (about
+                                  2^-11, a lower-precision step 1 in the sense of
+                                  Sec. 6, Figs. 6.2-6.3)                           */
 } mpj_options;
+
+/* mpj_options.flags */
+#define MPJ_OPT_SIMT_STAGE1   1   /* FP32 stage on the SIMT engine (no tensor cores)      */
+#define MPJ_OPT_SIMT_SWEEPS   2   /* FP64 sweeps on the SIMT engine (double-float / FP64
+                                     tile products instead of the tensor cores)           */
+#define MPJ_OPT_FP64_PRODUCTS 4   /* congruence, MGS panel projections and C = A Q as FP64
+                                     GEMMs instead of exactly split tensor-core products  */
+#define MPJ_OPT_FULL_INNER    8   /* tensor-core FP64 sweeps: full tournament inside each
+                                     block solve instead of the cross-pair schedule       */
+#define MPJ_OPT_MGS_GLOBAL   16   /* MGS panels from global memory instead of the shared
+                                     memory of a thread-block cluster                     */
+#define MPJ_OPT_TRACE        32   /* per-sweep rotation counts and off-norms on stderr    */
 
 /* ------------------------------------------------------------------------
  * Symmetric eigendecomposition A = V diag(Lambda) V^T.

@@ -61,10 +61,21 @@ class Stats(ctypes.Structure):
 
 
 class Options(ctypes.Structure):
-    """Mirror of ``mpj_options`` (zero fields mean 'default')."""
+    """Mirror of ``mpj_options`` (zero fields mean 'default'); ``flags`` takes the
+    OPT_* bits below."""
     _fields_ = [("max_sweeps", ctypes.c_int), ("max_sweeps_stage1", ctypes.c_int),
                 ("max_inner", ctypes.c_int), ("tol_stage1", ctypes.c_double),
-                ("ju_ratio", ctypes.c_double), ("block", ctypes.c_int)]
+                ("ju_ratio", ctypes.c_double), ("block", ctypes.c_int),
+                ("flags", ctypes.c_int), ("stage1_tf32_terms", ctypes.c_int)]
+
+
+# mpj_options.flags (include/mpjacobi.h)
+OPT_SIMT_STAGE1 = 1
+OPT_SIMT_SWEEPS = 2
+OPT_FP64_PRODUCTS = 4
+OPT_FULL_INNER = 8
+OPT_MGS_GLOBAL = 16
+OPT_TRACE = 32
 
 
 class BatchTuning(ctypes.Structure):

@@ -181,7 +181,7 @@ int stage1_evd(const double* A, int lda, int n, int N, int B, double normA, cons
                EvdBufs& b, SweepResult* r1, cudaStream_t s) {
     MPJ_TRY(copy_pad_f32(A, lda, n, n, b.T32, N, N, N, false, s));
     MPJ_TRY(set_identity_f32(b.V32, N, N, N, s));
-    const bool tc = B == 32 && tc_enabled();
+    const bool tc = B == 32 && !knobs().simt_stage1;
     if (tc) {
         // tensor-core engine: V32 holds V row-major; the FP64 T buffer (unused until
         // step 3) is the scratch P of its two passes
@@ -213,6 +213,7 @@ int check_evd_args(const double* A, int n, int lda, const void* L, const void* V
 int syevj_impl(bool mp, const double* A, int n, int lda, double* Lambda, double* V, int ldv,
                double tol, const mpj_options* opts, mpj_stats* st, void* work, size_t work_bytes,
                void* stream) {
+    KnobScope knob_scope(opts);
     if (st) memset(st, 0, sizeof(*st));
     MPJ_TRY(check_evd_args(A, n, lda, Lambda, V, ldv, tol));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -257,7 +258,7 @@ int syevj_impl(bool mp, const double* A, int n, int lda, double* Lambda, double*
         MPJ_TRY(set_identity_f64(b.V64, N, N, N, s));
         tm.mark(1); tm.mark(2); tm.mark(3);
     }
-    MPJ_TRY(twosided_sweeps<double>(b.T64, b.V64, N, n, fp64_block(B), tol * normA, kU, op.max_sweeps,
+    MPJ_TRY(twosided_sweeps<double>(b.T64, b.V64, N, n, B, tol * normA, kU, op.max_sweeps,
                                     op.max_inner, b.eng, s, &r2));                          // step 4
     MPJ_TRY(diag_to_f64(b.T64, true, N, n, b.sc.d, s));
     MPJ_TRY(rank_sort(b.sc.d, 1, n, false, b.sc.perm, s));
@@ -321,6 +322,7 @@ size_t svd_bytes(int m, int n, bool mp, const mpj_options* o) {
 int gesvj_impl(bool mp, const double* A, int m, int n, int lda, double* Sigma, double* U, int ldu,
                double* V, int ldv, double tol, const mpj_options* opts, mpj_stats* st, void* work,
                size_t work_bytes, void* stream) {
+    KnobScope knob_scope(opts);
     if (st) memset(st, 0, sizeof(*st));
     if (!A || !Sigma || !U || !V || n < 1 || m < n || lda < m || ldu < m || ldv < n || !(tol > 0) ||
         !std::isfinite(tol)) {
@@ -440,6 +442,7 @@ size_t mpj_gesvj_workspace_bytes(int m, int n) {
 int mpj_stage1_syevj32(const double* A, int n, int lda, double* Z, int ldz, double* D,
                        const mpj_options* opts, mpj_stats* st, void* work, size_t work_bytes,
                        void* stream) {
+    KnobScope knob_scope(opts);
     if (st) memset(st, 0, sizeof(*st));
     if (!A || !Z || !D || n < 1 || lda < n || ldz < n) { set_error_msg("invalid argument"); return MPJ_BAD_ARG; }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -552,6 +555,7 @@ size_t mpj_sweeps_workspace_bytes(int n) {
 int mpj_sweeps(double* T, int ldt, double* P, int ldp, int n, double tol, double normA,
                const mpj_options* opts, mpj_stats* st, void* work, size_t work_bytes,
                void* stream) {
+    KnobScope knob_scope(opts);
     if (st) memset(st, 0, sizeof(*st));
     if (!T || !P || n < 1 || ldt < n || ldp < n || !(tol > 0) || !(normA >= 0)) {
         set_error_msg("invalid argument");

@@ -86,6 +86,26 @@ struct SideStream {
     ~SideStream();
 };
 
+// ---------------------------------------------------------------- per-call switches
+// The path switches of mpj_options (flags, stage1_tf32_terms) for the call in
+// progress on this thread: KnobScope sets them at the entry of a C-ABI call and
+// restores the previous ones on return; without a scope they are the defaults.
+struct Knobs {
+    bool simt_stage1 = false;   // FP32 stage on the SIMT engine
+    bool simt_sweeps = false;   // FP64 sweeps on the SIMT engine
+    bool fp64_products = false; // FP64-pipe GEMMs instead of exactly split products
+    bool full_inner = false;    // tensor-core FP64 sweeps: full inner tournament
+    bool mgs_global = false;    // MGS panels from global memory
+    bool trace = false;         // per-sweep trace on stderr
+    int stage1_terms = 3;       // TF32 products per tile of the FP32 stage: 3 or 1
+};
+const Knobs& knobs();
+struct KnobScope {
+    Knobs saved;
+    explicit KnobScope(const mpj_options* o);
+    ~KnobScope();
+};
+
 // ---------------------------------------------------------------- profiling
 // Kernel classes counted (and, when enabled, timed with CUDA events on the
 // launching stream) by ProfScope; names in prof.cu.
@@ -103,16 +123,13 @@ struct ProfScope {
     ~ProfScope();
 };
 void prof_flush();
-// Per-sweep trace on stderr (rotation counts, off-norms) when MPJ_TRACE is set.
-bool trace_on();
+// Per-sweep trace on stderr (rotation counts, off-norms): MPJ_OPT_TRACE.
+inline bool trace_on() { return knobs().trace; }
 #define MPJ_PROF(cls, stream) ::mpj::ProfScope _mpj_prof_scope((cls), (stream))
 
 // ---------------------------------------------------------------- shapes
 inline int round_up(int x, int m) { return (x + m - 1) / m * m; }
 int choose_block(int n, const mpj_options* o);
-int fp64_block(int B);
-size_t solve_smem(size_t need);
-bool v_after_t(bool tc32);
 
 // ---------------------------------------------------------------- engines
 // Two-sided block Jacobi (Alg. 3.2 / step 4 of Alg. 4.1, parallel round-robin
@@ -149,10 +166,9 @@ int twosided_sweeps_tc64(double* T, double* V, int N, int n, double tol_abs, dou
 // Z[:, c] = V[:, perm[c]] (widened) from a row-major V.
 int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double* Z, int ldz,
                         cudaStream_t s);
-// The tensor-core engine is used for b = 32 unless MPJ_TC=0 (comparison switch).
-bool tc_enabled();
-// Inner schedule of the block solves (1: cross pairs, see inner_jacobi).
-int cross_schedule(bool fp64);
+// Inner schedule of the block solves (1: cross pairs, see inner_jacobi) of the
+// FP32 stage, the SIMT FP64 engine and the tensor-core FP64 engine.
+int cross_schedule(bool fp64, bool tc64);
 
 // One-sided block Jacobi (Alg. 5.1 / steps 4-10 of Alg. 5.2) on C (m x N, ld = ldc)
 // and V (N x N, ld = N).
@@ -185,8 +201,8 @@ struct OzOperand {
 size_t oz_operand_bytes(int rows, int K);
 int oz_operand(void* base, int rows, int K, OzOperand* op);
 bool oz_supported(int M, int N, int K);
-// MPJ_OZAKI=0 keeps every FP64 product on the FP64 pipe (comparison switch).
-bool oz_enabled();
+// Exactly split products unless MPJ_OPT_FP64_PRODUCTS keeps them on the FP64 pipe.
+inline bool oz_enabled() { return !knobs().fp64_products; }
 // Slice rows: row r is X[r * row_stride + k * k_stride], k < K (k_stride 1 or the
 // rows of a column-major matrix, row_stride 1).
 int oz_slice(const double* X, long long row_stride, long long k_stride, int rows, int K, OzOperand* op,

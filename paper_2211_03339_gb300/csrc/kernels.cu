@@ -114,35 +114,28 @@ int choose_block(int n, const mpj_options* o) {
     return n <= 256 ? 16 : 32;
 }
 
-// Dynamic shared memory of a block-solve launch: `need`, or 160 KB when
-// MPJ_SOLVE_EXCL=1, so that no tile-update CTA of the side stream (70-96 KB)
-// fits beside a solve CTA on its SM.
-size_t solve_smem(size_t need) {
-    static const bool excl = [] { const char* e = std::getenv("MPJ_SOLVE_EXCL"); return e && *e == '1'; }();
-    const size_t x = 160 * 1024;
-    return excl && need < x ? x : need;
+// ------------------------------------------------------------------ per-call switches
+namespace {
+thread_local Knobs g_knobs;
 }
 
-// Where the V stream joins a round: after the block solves, or after the T
-// update, so that the V update overlaps only the next round's solves and not
-// the T passes.  MPJ_V_AFTER_T is a bit mask: bit 1 the tensor-core FP32 stage,
-// bit 2 the two-sided engine.  Default 1: measured at n = 4096, the FP32 stage's
-// V pass after pass 2 saves 14 ms (pass 2 no longer shares the SMs with it),
-// while the FP64 V update after the tile update costs 5 ms.
-bool v_after_t(bool tc32) {
-    static const int mask = [] { const char* e = std::getenv("MPJ_V_AFTER_T"); return e ? atoi(e) : 1; }();
-    return (mask & (tc32 ? 1 : 2)) != 0;
+const Knobs& knobs() { return g_knobs; }
+
+KnobScope::KnobScope(const mpj_options* o) : saved(g_knobs) {
+    Knobs k;
+    if (o) {
+        k.simt_stage1 = (o->flags & MPJ_OPT_SIMT_STAGE1) != 0;
+        k.simt_sweeps = (o->flags & MPJ_OPT_SIMT_SWEEPS) != 0;
+        k.fp64_products = (o->flags & MPJ_OPT_FP64_PRODUCTS) != 0;
+        k.full_inner = (o->flags & MPJ_OPT_FULL_INNER) != 0;
+        k.mgs_global = (o->flags & MPJ_OPT_MGS_GLOBAL) != 0;
+        k.trace = (o->flags & MPJ_OPT_TRACE) != 0;
+        if (o->stage1_tf32_terms == 1 || o->stage1_tf32_terms == 3) k.stage1_terms = o->stage1_tf32_terms;
+    }
+    g_knobs = k;
 }
 
-// Block size of the FP64 sweeps of the EVD: the stage-1 size B unless
-// MPJ_B64=16 asks for b = 16 there (N stays a multiple of 2B, so of 32).
-int fp64_block(int B) {
-    static const int forced = [] {
-        const char* e = std::getenv("MPJ_B64");
-        return e && std::atoi(e) == 16 ? 16 : 0;
-    }();
-    return forced ? forced : B;
-}
+KnobScope::~KnobScope() { g_knobs = saved; }
 
 // ------------------------------------------------------------------ copies
 template <class Out>

@@ -194,7 +194,7 @@ static int panel_cluster_size(size_t smem) {
 // One 32-column panel: the shared-memory kernel when the panel's rows fit the
 // cluster's shared memory, else the global-memory kernel.
 static int mgs_panel(double* Q, int m, int ldq, int j0, int pb, int* d_flag, cudaStream_t s) {
-    static const bool smem_off = [] { const char* e = std::getenv("MPJ_MGS_SMEM"); return e && *e == '0'; }();
+    const bool smem_off = knobs().mgs_global;
     int cl = 0;
     int rows_per = 0;
     size_t smem = 0;

@@ -239,15 +239,8 @@ static int launch_round1(Real* C, int ldc, Real* V, int m, int N, Real* Wbuf, Re
 }
 
 // Fraction of N below which a sweep's rotation count turns the compensated
-// Gram on (0: only once a sweep passes the stopping rule).  MPJ_GRAM_COMP_SWITCH
-// overrides it (a negative value disables compensation); used to compare the
-// schedules on the same inputs.
+// Gram on (0: only once a sweep passes the stopping rule).
 constexpr double kCompSwitch = 0.0;
-static double comp_switch_override(double dflt) {
-    const char* e = std::getenv("MPJ_GRAM_COMP_SWITCH");
-    return e ? atof(e) : dflt;
-}
-
 template <class Real>
 int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, double tol_rot,
                     double ju_ratio, int max_sweeps, int max_inner, void* work, cudaStream_t s,
@@ -283,7 +276,7 @@ int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, doubl
     // sweep applies fewer than comp_switch * N rotations; comp_switch < 0
     // never, the first sweep that passes the rule ends the iteration).
     const bool dbl = sizeof(Real) == 8;
-    const double comp_switch = dbl ? comp_switch_override(kCompSwitch) : -1.0;
+    const double comp_switch = dbl ? kCompSwitch : -1.0;
     int comp = 0;
     while (res->sweeps < max_sweeps) {
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));

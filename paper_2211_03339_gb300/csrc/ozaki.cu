@@ -392,14 +392,6 @@ int oz_operand(void* base, int rows, int K, OzOperand* op) {
     return MPJ_SUCCESS;
 }
 
-bool oz_enabled() {
-    static const bool on = [] {
-        const char* e = std::getenv("MPJ_OZAKI");
-        return !(e && *e == '0');
-    }();
-    return on;
-}
-
 bool oz_supported(int M, int N, int K) { return M >= 1 && N >= 1 && K >= 1 && K <= 32768; }
 
 int oz_slice(const double* X, long long row_stride, long long k_stride, int rows, int K, OzOperand* op,

@@ -66,22 +66,6 @@ void prof_flush() {
     cudaGetLastError();   // cudaEventQuery's cudaErrorNotReady is not an error of ours
 }
 
-bool tc_enabled() {
-    static const bool on = [] {
-        const char* e = std::getenv("MPJ_TC");
-        return !(e && *e == '0');
-    }();
-    return on;
-}
-
-bool trace_on() {
-    static const bool on = [] {
-        const char* e = std::getenv("MPJ_TRACE");
-        return e && *e && *e != '0';
-    }();
-    return on;
-}
-
 }  // namespace mpj
 
 extern "C" {

@@ -19,10 +19,10 @@
 // Algorithms 59, 2012) cut from the FP64 bit patterns with integer operations:
 // with E_r the largest biased exponent of row r of X (of column c of F),
 //
-//   M = trunc(|x| 2^(1078 - E_r)) < 2^56,   M = sum_s a_s 2^(49 - 7 s),
-//   a_0 in [0, 128], a_s in [-64, 63] (s = 1..7, balanced digits),
+//   M = sign(x) trunc(|x| 2^(1078 - E_r)),  |M| < 2^56,  M = sum_s a_s 2^(49 - 7 s),
+//   |a_0| <= 128, a_s in [-64, 63] (s = 1..7, balanced digits),
 //
-// so x = +-2^(E_r - 1029) sum_s a_s 2^(-7 s) up to 2^(E_r - 1078) (every entry
+// so x = 2^(E_r - 1029) sum_s a_s 2^(-7 s) up to 2^(E_r - 1078) (every entry
 // within 2^3 of the row maximum is cut exactly).  Digits are exact in bf16 and
 // their products exact in FP32; the 36 slice products with s + t <= 7 are
 // accumulated per level d = s + t in eight FP32 TMEM accumulators (128 x 64
@@ -53,22 +53,26 @@ namespace {
 constexpr int kB = 32;                       // block size b
 constexpr int kM = 2 * kB;                   // pair width = K = N of the MMA
 constexpr int kSlab = 128;                   // tile rows = M of the MMA
-constexpr int kThr = 256;                    // pass kernel threads
+constexpr int kThr = 576;                    // pass kernel: 18 warps (see k_pass_tc64)
+constexpr int kSlicers = 256, kEpi = 256;    // threads of the slicer and epilogue roles
 constexpr int kS = 8;                        // digits (slices) per operand
 constexpr int kXBytes = kSlab * kM * 8;      // FP64 tile, 64 KB
 constexpr int kAPlane = kSlab * 128;         // A digit plane: 128 rows x 64 bf16
 constexpr int kBPlane = kM * 128;            // B digit plane: 64 rows x 64 bf16
-constexpr int kAGroup = 4;                   // A planes resident at a time
 constexpr int kFplBytes = kS * kBPlane + 256;   // per pair: 8 planes + 64 exponents
-constexpr int kOffA = kXBytes;
-constexpr int kOffB = kOffA + kAGroup * kAPlane;
-constexpr int kOffE = kOffB + kS * kBPlane;
-constexpr size_t kPassSmem = (size_t)kOffE + 256 + 1024;
-constexpr int kWait = 1 << 22;               // mbarrier polls before a CTA gives up
-// 64 at each of the seven lower 7-bit digit positions: adding it to M makes the
-// truncated base-128 digits of M + kBias minus 64 the balanced digits of M.
+constexpr int kOffX = 0;                     // two X stages
+constexpr int kOffA = 2 * kXBytes;           // two A plane slots
+constexpr int kOffB = kOffA + 2 * kAPlane;   // the 8 B planes and column exponents
+constexpr int kOffE = kOffB + kS * kBPlane;   // column exponents, one copy per X stage
+constexpr size_t kPassSmem = (size_t)kOffE + 2 * 256 + 1024;
+// 64 at each of the seven lower 7-bit digit positions and 256 at the top one:
+// for a signed M_s (|M_s| < 2^56), M_s + kBias is positive and below 2^58; its
+// base-128 digits (the top one 9 bits wide) minus 64 (minus 256 at the top) are
+// the balanced digits of M_s, M_s = sum_s d_s 2^(49 - 7 s), |d_0| <= 128,
+// d_s in [-64, 63].
 constexpr uint64_t kBias =
-    64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull);
+    64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull) +
+    (1ull << 57);
 
 // ---------------------------------------------------------------- slicing
 // Exponent class of x for a row maximum: 0 for x == 0, else max(E, 1) with E the
@@ -81,49 +85,29 @@ __device__ __forceinline__ int exp_class(double x) {
     return E ? E : nz;
 }
 
-// M + kBias for M = trunc(|x| 2^(1078 - Er)) (Er >= exp_class(x)), and the sign.
-__device__ __forceinline__ uint64_t scaled_mag(double x, int Er, uint32_t& neg) {
+// M_s + kBias for M_s = sign(x) trunc(|x| 2^(1078 - Er)), Er >= exp_class(x).
+__device__ __forceinline__ uint64_t scaled_signed(double x, int Er) {
     const uint64_t b = (uint64_t)__double_as_longlong(x);
-    neg = (uint32_t)(b >> 63);
     const int E = (int)((b >> 52) & 0x7FF);
     uint64_t mant = b & 0xFFFFFFFFFFFFFull;
     if (E) mant |= 1ull << 52;
     const int sh = (E ? E : 1) - Er + 3;          // <= 3
     const uint64_t M = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
-    return M + kBias;
+    const uint64_t sm = (uint64_t)((long long)b >> 63);   // all ones for a negative x
+    return ((M ^ sm) - sm) + kBias;
 }
 
-// Digits S0 .. S0+NP-1 of 8 consecutive elements as NP 16-byte chunks of bf16
-// (element e in halfword e).  A digit r becomes a float through the magic
-// constant 2^23 (exact), its bias is subtracted, and the bf16 is the float's
-// upper half (exact: at most 8 significant bits); sg holds the sign bits of the
-// element pairs.
-template <int S0, int NP>
-__device__ __forceinline__ void digits8(const uint64_t (&Mb)[8], const uint32_t (&sg)[4], uint4 (&out)[NP]) {
-#pragma unroll
-    for (int p = 0; p < NP; ++p) {
-        const int s = S0 + p;
-        const int shift = 49 - 7 * s;
-        const float K = s == 0 ? 8388608.0f : 8388672.0f;      // 2^23 + bias
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            uint32_t r0 = (uint32_t)(Mb[2 * q] >> shift), r1 = (uint32_t)(Mb[2 * q + 1] >> shift);
-            if (s > 0) { r0 &= 127u; r1 &= 127u; }
-            const float v0 = __fsub_rn(__uint_as_float(0x4B000000u | r0), K);
-            const float v1 = __fsub_rn(__uint_as_float(0x4B000000u | r1), K);
-            w[q] = __byte_perm(__float_as_uint(v0), __float_as_uint(v1), 0x7632) ^ sg[q];
-        }
-        out[p] = make_uint4(w[0], w[1], w[2], w[3]);
-    }
+// Digit s of a biased value as an exact float: the raw field (9 bits at the top
+// digit, 7 below) through the magic constant 2^23, minus 2^23 and the bias.
+__device__ __forceinline__ float digit_f(uint64_t v, int s) {
+    const uint32_t r = (uint32_t)(v >> (49 - 7 * s)) & (s == 0 ? 0x1FFu : 0x7Fu);
+    return __fsub_rn(__uint_as_float(0x4B000000u | r), s == 0 ? 8388864.0f : 8388672.0f);
 }
 
-__device__ __forceinline__ void prep8(const double (&x)[8], int Er, uint64_t (&Mb)[8], uint32_t (&sg)[4]) {
-    uint32_t ng[8];
-#pragma unroll
-    for (int e = 0; e < 8; ++e) Mb[e] = scaled_mag(x[e], Er, ng[e]);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sg[q] = (ng[2 * q] << 15) | (ng[2 * q + 1] << 31);
+// bf16 pair of digit s of two elements (e0 in the low half): the floats are
+// small integers, so their upper halves are exact bf16.
+__device__ __forceinline__ uint32_t digit_pair(uint64_t v0, uint64_t v1, int s) {
+    return __byte_perm(__float_as_uint(digit_f(v0, s)), __float_as_uint(digit_f(v1, s)), 0x7632);
 }
 
 // Byte offset of 16-byte chunk j (elements 8j..8j+7 along K) of row r in a
@@ -133,18 +117,32 @@ __device__ __forceinline__ int sw_chunk(int r, int j) {
 }
 
 // The eight levels T_d (exact integers in FP32, |T_d| < 2^22) as one 64-bit
-// integer sum_d T_d 2^(42 - 7 d) (T_7 truncated by 2^-7): each float becomes
-// its integer through the magic constant 1.5 * 2^23.
+// integer sum_d T_d 2^(42 - 7 d) (T_7 truncated by 2^-7).  A float v with
+// |v| < 2^22 added to 1.5 * 2^23 has the bit pattern 0x4B400000 + v, so the
+// lower levels are summed as bit patterns with 32 x 32 -> 64-bit multiply-adds
+// and the constant part is removed once; the two upper levels go into the
+// upper word.
 __device__ __forceinline__ long long combine8(const float (&a)[8]) {
-    int t[8];
+    constexpr unsigned long long kMagic = 0x4B400000ull;
+    uint32_t u[8];
 #pragma unroll
-    for (int d = 0; d < 8; ++d) t[d] = __float_as_int(__fadd_rn(a[d], 12582912.0f)) - 0x4B400000;
-    return ((long long)t[0] << 42) + ((long long)t[1] << 35) + ((long long)t[2] << 28) +
-           ((long long)t[3] << 21) + ((long long)t[4] << 14) + ((long long)t[5] << 7) + (long long)t[6] +
-           (long long)(t[7] >> 7);
+    for (int d = 0; d < 8; ++d) u[d] = __float_as_uint(__fadd_rn(a[d], 12582912.0f));
+    // levels 2..6 as bit patterns: sum u_d 2^(42 - 7 d) < 2^60; level 7 truncated
+    unsigned long long lo = (unsigned long long)(u[7] >> 7);
+    lo += (unsigned long long)u[6];
+    lo += (unsigned long long)u[5] << 7;
+    lo += (unsigned long long)u[4] << 14;
+    lo += (unsigned long long)u[3] << 21;
+    lo += (unsigned long long)u[2] << 28;
+    constexpr unsigned long long kLoConst = (kMagic >> 7) + kMagic + (kMagic << 7) + (kMagic << 14) +
+                                            (kMagic << 21) + (kMagic << 28);
+    const long long t0 = (long long)u[0] - (long long)kMagic, t1 = (long long)u[1] - (long long)kMagic;
+    return (long long)(lo - kLoConst) + (t0 << 42) + (t1 << 35);
 }
 
-// y = x + 2^(Er + Ec - 2100) S.
+// y = x + 2^(Er + Ec - 2100) S: the integer rounded to FP64 once, then one FMA
+// with the exact power of two.  (An all-integer conversion that leaves a single
+// FP64 addition measured slower: the FP64 unit is not the tile's limit.)
 __device__ __forceinline__ double apply_level_sum(double x, long long S, int Er, int Ec) {
     if (S == 0) return x;
     const int be = Er + Ec - 1077;                   // biased exponent of the scale
@@ -153,14 +151,11 @@ __device__ __forceinline__ double apply_level_sum(double x, long long S, int Er,
     return x + scalbn(v, be - 1023);                 // tiny operands: not on the fast path
 }
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7])
-                 : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float& v0, float& v1) {
+    uint32_t r0, r1;
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(taddr));
+    v0 = __uint_as_float(r0);
+    v1 = __uint_as_float(r1);
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
@@ -215,13 +210,14 @@ k_solve2_tc64(double* __restrict__ T, int N, double* __restrict__ Fbuf, double* 
     cls = max(cls, __shfl_xor_sync(0xffffffffu, cls, 2));
     cls = max(cls, __shfl_xor_sync(0xffffffffu, cls, 4));
     if (j == 0) reinterpret_cast<int*>(dst + kS * kBPlane)[c] = cls;
-    uint64_t Mb[8];
-    uint32_t sg[4];
-    prep8(x, cls, Mb, sg);
-    uint4 d[kS];
-    digits8<0, kS>(Mb, sg, d);
+    uint64_t v[8];
 #pragma unroll
-    for (int p = 0; p < kS; ++p) *reinterpret_cast<uint4*>(dst + p * kBPlane + sw_chunk(c, j)) = d[p];
+    for (int e = 0; e < 8; ++e) v[e] = scaled_signed(x[e], cls);
+#pragma unroll
+    for (int p = 0; p < kS; ++p)
+        *reinterpret_cast<uint4*>(dst + p * kBPlane + sw_chunk(c, j)) =
+            make_uint4(digit_pair(v[0], v[1], p), digit_pair(v[2], v[3], p), digit_pair(v[4], v[5], p),
+                       digit_pair(v[6], v[7], p));
 }
 
 // ---------------------------------------------------------------- pass kernel
@@ -250,11 +246,71 @@ __device__ __forceinline__ void tile_io(const CUtensorMap* map, bool load, unsig
     }
 }
 
-// One CTA per SM (the eight accumulators take the whole TMEM).  Items are
-// (slab s, pair b), b-major; CTA k takes items [k per_cta, (k+1) per_cta), so
-// that the digit planes of F_b are reloaded only when the pair changes.  With
-// skip_identity, items whose W_b is the identity are skipped (in place V);
-// otherwise they are copied.  With Sbuf, rows in IJ_b take the solver's block.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
+// Named barrier over `count` threads that also ORs a predicate across them, so
+// that every thread of a role takes the same decision.
+__device__ __forceinline__ bool bar_or(int id, int count, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n.reg .pred pi, po;\nsetp.ne.u32 pi, %1, 0;\nbar.red.or.pred po, %2, %3, pi;\nselp.u32 %0, 1, 0, po;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+
+// Wait for phase `parity` of an mbarrier, suspending the thread in the
+// barrier unit between polls (suspend-time hint 20 us) instead of spinning.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, int polls) {
+    uint32_t done = 0;
+    for (int it = 0; it < polls && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(tc::smem_u32(bar)), "r"(parity), "r"(20000u)
+            : "memory");
+    }
+    return done != 0;
+}
+
+// Bounded wait (about two seconds at most) that gives up early once another
+// role has recorded a failure.
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, volatile int* failed) {
+    for (int r = 0; r < 100; ++r) {
+        if (mbar_wait_sleep(bar, parity, 1000)) return true;
+        if (*failed) return false;
+    }
+    *failed = 1;
+    return false;
+}
+
+__device__ __forceinline__ bool item_taken(int it, int n_slabs, int skip_identity, const float* __restrict__ fmax,
+                                           int& b, int& s) {
+    b = it / n_slabs;
+    s = it - b * n_slabs;
+    return !(skip_identity && fmax[b] == 0.f);
+}
+
+// Warp-specialised, software-pipelined pass (one CTA per SM; the eight level
+// accumulators take the whole TMEM):
+//   warp 0     producer: TMA loads of the FP64 tiles into a 2-stage ring, and
+//              the digit planes of F_b (one bulk copy) when the pair changes;
+//   warp 1     MMA issuer (one thread): for each digit plane s of the tile the
+//              products (s, t), t <= 7 - s, into the level accumulators s + t;
+//   warps 2-9  slicers: per tile row, the row exponent class, then the 8 digit
+//              planes one by one into a 2-slot ring;
+//   warps 10-17 epilogue: the levels of its 32 columns folded into 64-bit
+//              integers (TMEM is then released to the next tile's MMAs), then
+//              y = x + 2^e S in place in the tile's stage and one TMA store.
+// Items are (slab s, pair b), b-major; CTA k takes items [k per_cta, (k+1)
+// per_cta).  With skip_identity, items whose W_b is the identity are skipped
+// (in place V); otherwise they are copied.  With Sbuf, rows in IJ_b take the
+// solver's rotated block.  Every wait is bounded: a timeout sets *err and the
+// roles leave their loops.
 template <bool kLr>
 __global__ void __launch_bounds__(kThr, 1)
 k_pass_tc64(const __grid_constant__ Tc64Maps maps, int N, int n_slabs, int total, int per_cta,
@@ -263,164 +319,201 @@ k_pass_tc64(const __grid_constant__ Tc64Maps maps, int N, int n_slabs, int total
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                                          ~uintptr_t(1023));
-    unsigned char* Xs = sm;
+    unsigned char* Xst = sm + kOffX;
     unsigned char* Ap = sm + kOffA;
     unsigned char* Bp = sm + kOffB;
-    const int* exc = reinterpret_cast<const int*>(sm + kOffE);
-    __shared__ __align__(8) uint64_t bar_ld, bar_mma;
+    unsigned char* Ec = sm + kOffE;                 // stage st: 64 ints at Ec + 256 st
+    __shared__ __align__(8) uint64_t xfull[2], xempty[2], afull[2], aempty[2], rowx[2], accfull, accempty;
     __shared__ uint32_t tmem_slot;
-    __shared__ int exr[kSlab];
+    __shared__ int exr[2][kSlab];
+    __shared__ volatile int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nblocks = N / kB;
     if (tid == 0) {
-        tc::mbar_init(&bar_ld, 1);
-        tc::mbar_init(&bar_mma, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&xfull[i], 1);
+            tc::mbar_init(&xempty[i], 1);
+            tc::mbar_init(&afull[i], kSlicers);
+            tc::mbar_init(&aempty[i], 1);
+            tc::mbar_init(&rowx[i], kSlicers);
+        }
+        tc::mbar_init(&accfull, 1);
+        tc::mbar_init(&accempty, kEpi);
         tc::fence_mbar_init();
+        failed = 0;
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 512);
+    if (warp == 1) tc::tmem_alloc(&tmem_slot, 512);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
     const int it0 = blockIdx.x * per_cta;
     const int it1 = min(total, it0 + per_cta);
-    int cur = -1;                                   // pair whose F planes are in Bp
-    uint32_t pl = 0, pm = 0;                        // mbarrier phases
-    bool failed = false;
-    // slicing items of this thread: row ms = tid % 128, chunks js = tid / 128 + 2 i
-    const int ms = tid & (kSlab - 1), jh = tid >> 7;
-    for (int it = it0; it < it1 && !failed; ++it) {
-        const int b = it / n_slabs, s = it % n_slabs;
-        const bool ident = fmax[b] == 0.f;
-        if (ident && skip_identity) continue;
-        int I, J;
-        round_pair(round, b, nblocks, I, J);
-        const int row0 = s * kSlab;
-        const bool loadF = !ident && b != cur;
-        if (tid < kSlab) exr[tid] = 0;
-        if (tid == 0) {
-            tc::mbar_expect_tx(&bar_ld, kXBytes + (loadF ? kFplBytes : 0));
-            if (loadF) bulk_load(Bp, Fpl + (size_t)b * kFplBytes, kFplBytes, &bar_ld);
-            tile_io<kLr>(&maps.in, true, Xs, row0, I, J, &bar_ld);
-        }
-        if (loadF) cur = b;
-        bool ok = tc::mbar_wait(&bar_ld, pl, kWait);
-        pl ^= 1;
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-        if (!ident) {
-            double xv[4][8];
-            int emax = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    xv[i][e] = *reinterpret_cast<const double*>(Xs + xoff<kLr>(ms, 8 * (jh + 2 * i) + e));
-                    emax = max(emax, exp_class(xv[i][e]));
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            int k = 0, cur = -1;
+            for (int it = it0; it < it1; ++it) {
+                int b, s;
+                if (!item_taken(it, n_slabs, skip_identity, fmax, b, s)) continue;
+                const int st = k & 1;
+                if (k >= 2 && !wait_or_fail(&xempty[st], ((k >> 1) - 1) & 1, &failed)) break;
+                const bool needF = b != cur;
+                // the B planes are overwritten only once the previous tile's MMAs are done
+                if (needF && k >= 1 && !wait_or_fail(&accfull, (k - 1) & 1, &failed)) break;
+                int I, J;
+                round_pair(round, b, nblocks, I, J);
+                // the exponents go with every tile (the epilogue of the previous tile of
+                // this stage has released them); the planes only when the pair changes
+                const unsigned char* src = Fpl + (size_t)b * kFplBytes;
+                tc::mbar_expect_tx(&xfull[st], kXBytes + 256 + (needF ? kS * kBPlane : 0));
+                bulk_load(Ec + 256 * st, src + kS * kBPlane, 256, &xfull[st]);
+                if (needF) {
+                    bulk_load(Bp, src, kS * kBPlane, &xfull[st]);
+                    cur = b;
                 }
-            atomicMax(&exr[ms], emax);
-            __syncthreads();
-            const int Er = exr[ms];
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                if (g == 1) {                       // the A planes are free once group 0's MMAs are done
-                    ok = tc::mbar_wait(&bar_mma, pm, kWait);
-                    pm ^= 1;
-                    tc::fence_after_sync();
-                    if (__syncthreads_or(!ok)) { failed = true; break; }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    uint64_t Mb[8];
-                    uint32_t sg[4];
-                    prep8(xv[i], Er, Mb, sg);
-                    uint4 d[kAGroup];
-                    if (g == 0) digits8<0, kAGroup>(Mb, sg, d);
-                    else digits8<kAGroup, kAGroup>(Mb, sg, d);
-                    const int off = sw_chunk(ms, jh + 2 * i);
-#pragma unroll
-                    for (int p = 0; p < kAGroup; ++p) *reinterpret_cast<uint4*>(Ap + p * kAPlane + off) = d[p];
-                }
-                tc::fence_proxy_async();
-                tc::fence_before_sync();
-                __syncthreads();
-                tc::fence_after_sync();
-                if (tid == 0) {
-                    constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, kSlab, kM);
-                    const uint32_t a0 = tc::smem_u32(Ap), b0 = tc::smem_u32(Bp);
-#pragma unroll
-                    for (int sl = 0; sl < kAGroup; ++sl) {
-                        const int sa = g * kAGroup + sl;
-#pragma unroll
-                        for (int t = 0; t + sa < kS; ++t)
-#pragma unroll
-                            for (int ks = 0; ks < kM / 16; ++ks)
-                                tc::mma_f16(tmem + (uint32_t)((sa + t) * kM),
-                                            tc::smem_desc_sw128(a0 + sl * kAPlane + ks * 32),
-                                            tc::smem_desc_sw128(b0 + t * kBPlane + ks * 32), idesc,
-                                            (sa == 0 && ks == 0) ? 0u : 1u);
-                    }
-                    tc::commit(&bar_mma);
-                }
+                tile_io<kLr>(&maps.in, true, Xst + st * kXBytes, s * kSlab, I, J, &xfull[st]);
+                ++k;
             }
-            if (failed) break;
-            ok = tc::mbar_wait(&bar_mma, pm, kWait);
-            pm ^= 1;
-            tc::fence_after_sync();
-            if (__syncthreads_or(!ok)) { failed = true; break; }
         }
-        // epilogue: thread (warp w, lane) = tile row m = 32 (w % 4) + lane (its TMEM
-        // lane), columns 32 (w / 4) .. +31
-        {
-            const int m = 32 * (warp & 3) + lane;
-            const int cb = 32 * (warp >> 2);
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, kSlab, kM);
+            const uint32_t b0 = tc::smem_u32(Bp);
+            int k = 0;
+            uint32_t q = 0;
+            bool ok = true;
+            for (int it = it0; it < it1 && ok; ++it) {
+                int b, s;
+                if (!item_taken(it, n_slabs, skip_identity, fmax, b, s)) continue;
+                if (k >= 1 && !wait_or_fail(&accempty, (k - 1) & 1, &failed)) break;
+                tc::fence_after_sync();
+                for (int sa = 0; sa < kS; ++sa, ++q) {
+                    const int slot = q & 1;
+                    if (!wait_or_fail(&afull[slot], (q >> 1) & 1, &failed)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    const uint32_t a0 = tc::smem_u32(Ap + slot * kAPlane);
+                    for (int t = 0; t + sa < kS; ++t)
+#pragma unroll
+                        for (int ks = 0; ks < kM / 16; ++ks)
+                            tc::mma_f16(tmem + (uint32_t)((sa + t) * kM), tc::smem_desc_sw128(a0 + ks * 32),
+                                        tc::smem_desc_sw128(b0 + t * kBPlane + ks * 32), idesc,
+                                        (sa == 0 && ks == 0) ? 0u : 1u);
+                    tc::commit(&aempty[slot]);
+                }
+                if (!ok) break;
+                tc::commit(&accfull);
+                ++k;
+            }
+        }
+    } else if (warp < 10) {
+        // ------------------------------------------------------------ slicers
+        // lane pair (2r, 2r+1) of warp w holds row m = 16 (w - 2) + r, halves h = 0, 1
+        const int m = 16 * (warp - 2) + (lane >> 1), h = lane & 1;
+        int k = 0;
+        uint32_t q = 0;
+        bool bad = false;
+        for (int it = it0; it < it1; ++it) {
+            int b, s;
+            if (!item_taken(it, n_slabs, skip_identity, fmax, b, s)) continue;
+            const int st = k & 1;
+            const bool ok = !bad && wait_or_fail(&xfull[st], (k >> 1) & 1, &failed);
+            if (bar_or(1, kSlicers, !ok)) break;
+            const unsigned char* X = Xst + st * kXBytes;
+            int cls = 0;
+#pragma unroll 8
+            for (int c = 0; c < 32; ++c)
+                cls = max(cls, exp_class(*reinterpret_cast<const double*>(X + xoff<kLr>(m, 32 * h + c))));
+            cls = max(cls, __shfl_xor_sync(0xffffffffu, cls, 1));
+            if (h == 0) exr[st][m] = cls;
+            mbar_arrive(&rowx[st]);
+            uint64_t Mb[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c)
+                Mb[c] = scaled_signed(*reinterpret_cast<const double*>(X + xoff<kLr>(m, 32 * h + c)), cls);
+#pragma unroll
+            for (int sp = 0; sp < kS; ++sp, ++q) {
+                const int slot = q & 1;
+                if (!bad && q >= 2 && !wait_or_fail(&aempty[slot], ((q >> 1) - 1) & 1, &failed)) bad = true;
+                if (!bad) {
+                    unsigned char* A = Ap + slot * kAPlane;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        *reinterpret_cast<uint4*>(A + sw_chunk(m, 4 * h + i)) = make_uint4(
+                            digit_pair(Mb[8 * i], Mb[8 * i + 1], sp), digit_pair(Mb[8 * i + 2], Mb[8 * i + 3], sp),
+                            digit_pair(Mb[8 * i + 4], Mb[8 * i + 5], sp), digit_pair(Mb[8 * i + 6], Mb[8 * i + 7], sp));
+                    tc::fence_proxy_async();
+                }
+                mbar_arrive(&afull[slot]);
+            }
+            ++k;
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int quarter = warp & 3;
+        const int m = 32 * quarter + lane;
+        const int cb = 32 * ((warp - 10) >> 2);
+        const uint32_t lanebase = tmem + ((uint32_t)(32 * quarter) << 16);
+        int k = 0;
+        for (int it = it0; it < it1; ++it) {
+            int b, s;
+            if (!item_taken(it, n_slabs, skip_identity, fmax, b, s)) continue;
+            const int st = k & 1;
+            bool ok = wait_or_fail(&accfull, k & 1, &failed);
+            ok = ok && wait_or_fail(&rowx[st], (k >> 1) & 1, &failed);
+            ok = ok && wait_or_fail(&xfull[st], (k >> 1) & 1, &failed);
+            tc::fence_after_sync();
+            if (bar_or(2, kEpi, !ok)) break;
+            int I, J;
+            round_pair(round, b, nblocks, I, J);
+            const int row0 = s * kSlab;
+            const int Er = exr[st][m];
+            long long S[32];
+#pragma unroll
+            for (int c = 0; c < 32; c += 2) {
+                float l0[kS], l1[kS];
+#pragma unroll
+                for (int d = 0; d < kS; ++d) tmem_ld2(lanebase + (uint32_t)(d * kM + cb + c), l0[d], l1[d]);
+                tc::tmem_wait_ld();
+                S[c] = combine8(l0);
+                S[c + 1] = combine8(l1);
+            }
+            tc::fence_before_sync();
+            mbar_arrive(&accempty);                  // TMEM is free for the next tile's MMAs
             const int row = row0 + m;
-            const int Er = exr[m];
             const double* Srow = nullptr;
             if (Sbuf) {
                 const int blk = row / kB;
                 if (blk == I) Srow = Sbuf + (size_t)b * kM * kM + (size_t)(row % kB) * kM;
                 else if (blk == J) Srow = Sbuf + (size_t)b * kM * kM + (size_t)(kB + row % kB) * kM;
             }
-            const uint32_t lanebase = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-#pragma unroll 1
-            for (int c0 = cb; c0 < cb + 32; c0 += 8) {
-                float a[kS][8];
-                if (!ident) {
+            unsigned char* X = Xst + st * kXBytes;
+            const int* exc = reinterpret_cast<const int*>(Ec + 256 * st);
 #pragma unroll
-                    for (int d = 0; d < kS; ++d) tmem_ld8(lanebase + (uint32_t)(d * kM + c0), a[d]);
-                    tc::tmem_wait_ld();
-                }
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int c = c0 + e;
-                    double* px = reinterpret_cast<double*>(Xs + xoff<kLr>(m, c));
-                    double y = *px;
-                    if (!ident) {
-                        float lv[kS];
-#pragma unroll
-                        for (int d = 0; d < kS; ++d) lv[d] = a[d][e];
-                        y = apply_level_sum(y, combine8(lv), Er, exc[c]);
-                    }
-                    if (Srow) y = Srow[c];
-                    *px = y;
-                }
+            for (int c = 0; c < 32; ++c) {
+                double* px = reinterpret_cast<double*>(X + xoff<kLr>(m, cb + c));
+                double y = apply_level_sum(*px, S[c], Er, exc[cb + c]);
+                if (Srow) y = Srow[cb + c];
+                *px = y;
             }
+            tc::fence_proxy_async();                 // the tile's generic writes -> TMA store
+            bar_or(2, kEpi, false);
+            if (tid == 10 * 32) {
+                tile_io<kLr>(&maps.out, false, X, row0, I, J, nullptr);
+                tc::bulk_commit();
+                tc::bulk_wait_read();
+                mbar_arrive(&xempty[st]);
+            }
+            ++k;
         }
-        tc::fence_proxy_async();                     // the tile's generic writes -> TMA store
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
-            tile_io<kLr>(&maps.out, false, Xs, row0, I, J, nullptr);
-            tc::bulk_commit();
-            tc::bulk_wait_read();                    // Xs is reloaded by the next item
-        }
+        if (tid == 10 * 32) tc::bulk_wait_all();
     }
-    if (failed && tid == 0) atomicExch(err, 1ull);
-    if (tid == 0) tc::bulk_wait_all();
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, 512);
+    if (failed && tid == 0) atomicExch(err, 1ull);
+    if (warp == 1) tc::tmem_dealloc(tmem, 512);
 }
 
 // ---------------------------------------------------------------- host side
@@ -511,7 +604,7 @@ int twosided_sweeps_tc64(double* T, double* V, int N, int n, double tol_abs, dou
     HostScratch hs;
     MPJ_TRY(hs.init());
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)solve_smem(InnerLayout<double, kM>::bytes)));
+                                      (int)InnerLayout<double, kM>::bytes));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc64<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
     Tc64Maps m1, m2, mv;
@@ -553,7 +646,7 @@ int twosided_sweeps_tc64(double* T, double* V, int N, int n, double tol_abs, dou
             if (set < 0) return MPJ_CUDA_ERROR;
             {
                 MPJ_PROF(PC_SOLVE2_F64, s);
-                k_solve2_tc64<<<K, kSolveThreads, solve_smem(InnerLayout<double, kM>::bytes), s>>>(
+                k_solve2_tc64<<<K, kSolveThreads, InnerLayout<double, kM>::bytes, s>>>(
                     T, N, Fbuf[set], Sbuf[set], Fpl[set], fmax[set], r, eps_skip, tau, gate, max_inner, xs, rot);
             }
             MPJ_LAUNCH_CHECK("k_solve2_tc64");

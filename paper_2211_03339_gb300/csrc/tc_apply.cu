@@ -121,7 +121,7 @@ __device__ __forceinline__ void issue_item(const PassMaps& maps, int it, int ite
 __global__ void __launch_bounds__(kTcThreads, 2)
 k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N, int n_slabs,
           int items_T, int total, const float* __restrict__ Sbuf, const float* __restrict__ fmax,
-          int round, unsigned long long* __restrict__ err) {
+          int round, int terms, unsigned long long* __restrict__ err) {
     extern __shared__ unsigned char smraw[];
     float* sl = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full;
@@ -180,9 +180,12 @@ k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N
                 const uint32_t xl = tc::smem_u32(Xl + ch * kChunk) + off;
                 const uint32_t fh = tc::smem_u32(F + ch * kFChunk) + off;
                 const uint32_t fl = tc::smem_u32(F + (2 + ch) * kFChunk) + off;
-                tc::mma_tf32(tmem, tc::smem_desc_sw128(xl), tc::smem_desc_sw128(fh), idesc, ks > 0);
-                tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fl), idesc, 1);
-                tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fh), idesc, 1);
+                if (terms == 3) {            // the two cross terms of the three-term split
+                    tc::mma_tf32(tmem, tc::smem_desc_sw128(xl), tc::smem_desc_sw128(fh), idesc, ks > 0);
+                    tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fl), idesc, 1);
+                }
+                tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fh), idesc,
+                             terms == 3 || ks > 0);
             }
             tc::commit(&mma_done);
         }
@@ -360,7 +363,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     HostScratch hs;
     MPJ_TRY(hs.init());
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2_nb, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)solve_smem(InnerLayout<float, kM>::bytes)));
+                                      (int)InnerLayout<float, kM>::bytes));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
     PassMaps maps1[2], maps2[2];                         // per buffer set: pass 1, pass 2 and V
     for (int set = 0; set < 2; ++set) {
@@ -389,8 +392,13 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     const int gridv = N >= 8192 ? items : grid1;
     const float tau = (float)(tol_abs / (double)N);
     const float gate = 1.0f / 4096.0f;                   // Newton-Schulz when some |F| >= 2^-12
-    const int cross = N >= kB * kB ? cross_schedule(false) : 0;     // see cross_schedule
-    const bool v_late = v_after_t(true);
+    // TF32 products per tile: 3 (about FP32 accuracy) or 1 (hi*hi only, about
+    // 2^-11: a lower-precision step 1, mpj_options.stage1_tf32_terms)
+    const int terms = knobs().stage1_terms;
+    const int cross = N >= kB * kB ? cross_schedule(false, false) : 0;     // see cross_schedule
+    // the V pass joins after pass 2, so that it overlaps only the next round's
+    // block solves (measured at n = 4096: stage 1 238 -> 223 ms)
+    const bool v_late = true;
     while (res->sweeps < max_sweeps) {
         if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
@@ -400,7 +408,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
             if (set < 0) return MPJ_CUDA_ERROR;
             {
                 MPJ_PROF(PC_SOLVE2_F32, s);
-                k_solve2_nb<<<K, kSolveThreads, solve_smem(InnerLayout<float, kM>::bytes), s>>>(
+                k_solve2_nb<<<K, kSolveThreads, InnerLayout<float, kM>::bytes, s>>>(
                     T, N, Wbuf[set], Sbuf[set], Fimg[set], fmax[set], r, (float)eps_skip, tau, gate, max_inner,
                     cross, rot);
             }
@@ -409,13 +417,13 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
             {
                 MPJ_PROF(PC_TC1_F32, s);
                 k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps1[set], P, N, n_slabs, items, items, nullptr,
-                                                               fmax[set], r, rot + 1);
+                                                               fmax[set], r, terms, rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc pass 1");
             {
                 MPJ_PROF(PC_TC2_F32, s);
                 k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps2[set], T, N, n_slabs, items, items, Sbuf[set],
-                                                               fmax[set], r, rot + 1);
+                                                               fmax[set], r, terms, rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc pass 2");
             if (v_late) MPJ_TRY(side.after_solve());
@@ -426,7 +434,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
                 // step 1 at n = 4096, 1443 vs 1352 ms at n = 8192).
                 MPJ_PROF(PC_TCV_F32, side.sv);
                 k_pass_tc<<<gridv, kTcThreads, kPassSmem, side.sv>>>(maps2[set], T, N, n_slabs, 0, items, nullptr,
-                                                                     fmax[set], r, rot + 1);
+                                                                     fmax[set], r, terms, rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc V");
             MPJ_TRY(side.after_v());

@@ -66,36 +66,25 @@ k_apply2V(Real* __restrict__ V, int N, const Real* __restrict__ Fbuf, const floa
 
 // Inner-sweep schedule of the block solves: the cross-pair schedule (inner_jacobi
 // with cross_round) for the FP32 sweeps of step 1, where it halves the steps of a
-// block solve at the same outer sweep count; the full tournament for the FP64
-// sweeps, where the cross schedule leaves larger block rotations on clustered
-// spectra (fewer tiles qualify for the double-float products).  MPJ_CROSS=0 / 1
-// forces one schedule everywhere, for comparisons.  The callers use it only
-// when an outer sweep has at least b - 1 rounds (N >= b^2), so that the intra
-// steps of the rounds of one sweep cover every pair inside a block.
-int cross_schedule(bool fp64) {
-    static const int forced = [] {
-        const char* e = std::getenv("MPJ_CROSS");
-        return e && (*e == '0' || *e == '1') ? *e - '0' : -1;
-    }();
-    return forced >= 0 ? forced : (fp64 ? 0 : 1);
+// block solve at the same outer sweep count, and for the tensor-core FP64 sweeps,
+// whose tile products do not depend on the size of the block rotations (measured
+// at n = 4096: uniform 547 -> 513 ms, clustered 1660 -> 1340 ms, equal or fewer
+// sweeps; MPJ_OPT_FULL_INNER restores the full tournament there).  The SIMT FP64
+// engine keeps the full tournament: the cross schedule leaves larger block
+// rotations on clustered spectra, so fewer of its tiles qualify for the
+// double-float products.  The callers use it only when an outer sweep has at
+// least b - 1 rounds (N >= b^2), so that the intra steps of the rounds of one
+// sweep cover every pair inside a block.
+int cross_schedule(bool fp64, bool tc64) {
+    if (!fp64) return 1;
+    return tc64 && !knobs().full_inner ? 1 : 0;
 }
 
-// Index of the first FP64 sweep run with b = 16 (2: the third sweep);
-// MPJ_LATE_B16=<k> moves it, a negative value keeps b = 32 throughout.
-static int late_b16_sweep() {
-    static const int k = [] {
-        const char* e = std::getenv("MPJ_LATE_B16");
-        return e ? atoi(e) : 2;
-    }();
-    return k;
-}
-
-// MPJ_DF_GATE overrides the double-float gate (a negative value disables the
-// double-float path); used to compare both arithmetics on the same inputs.
-static float df_gate_override(float dflt) {
-    const char* e = std::getenv("MPJ_DF_GATE");
-    return e ? (float)atof(e) : dflt;
-}
+// First FP64 sweep run with b = 16 on a nearly diagonal T in the SIMT engine (2:
+// the third sweep).
+constexpr int kLateB16Sweep = 2;
+// Double-float tile products when both block rotations have max |F| <= 2^-8.
+constexpr float kDfGate = 1.0f / 256.0f;
 
 template <class Real>
 size_t twosided_workspace_bytes(int N, int B) {
@@ -122,7 +111,7 @@ template <class Real, int B>
 static int configure_twosided() {
     constexpr int M = 2 * B;
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2<Real, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)solve_smem(InnerLayout<Real, M>::bytes)));
+                                      (int)InnerLayout<Real, M>::bytes));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_apply2T<Real, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)ApplySmem<Real, B>::t));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_apply2V<Real, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -139,11 +128,13 @@ static int launch_round(Real* T, Real* V, int N, Real* Wbuf, float* fmax, int r,
     const int K = N / M;
     const bool dbl = sizeof(Real) == 8;
     { MPJ_PROF(dbl ? PC_SOLVE2_F64 : PC_SOLVE2_F32, s);
-      k_solve2<Real, B><<<K, kSolveThreads, solve_smem(InnerLayout<Real, M>::bytes), s>>>(T, N, Wbuf, fmax, r, eps, tau,
-                                                                         gate, max_inner, N >= B * B ? cross_schedule(dbl) : 0, rot,
+      k_solve2<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(T, N, Wbuf, fmax, r, eps, tau,
+                                                                         gate, max_inner, N >= B * B ? cross_schedule(dbl, false) : 0, rot,
                                                                          Fsplit); }
     MPJ_LAUNCH_CHECK("k_solve2");
-    const bool v_late = v_after_t(false);
+    // the V update waits only for the block solve, so it overlaps the tile update as
+    // well (measured: waiting for the tile update costs 5 ms at n = 4096)
+    const bool v_late = false;
     if (!v_late) MPJ_TRY(side.after_solve());
     int n_ttiles = K * (K - 1) / 2;
     if (n_ttiles > 0) {
@@ -166,9 +157,9 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
                     int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res) {
     if constexpr (sizeof(Real) == 8) {
         // b = 32: the block rotations are applied on the tensor cores (tc64_apply.cu)
-        if (tc_enabled() && tc64_supported(N, B))
+        if (!knobs().simt_sweeps && tc64_supported(N, B))
             return twosided_sweeps_tc64(T, V, N, n, tol_abs, eps_skip, max_sweeps, max_inner,
-                                        cross_schedule(true), work, s, res);
+                                        cross_schedule(true, true), work, s, res);
     }
     const int M = 2 * B;
     const int K = N / M;
@@ -210,7 +201,7 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     // n = 4096: geometric 1644 -> 1529 ms, clustered 2803 -> 2739 ms; the plain
     // algorithm on a dense T took one sweep more with the switch, so it keeps b).
     // The b = 32 buffers hold the b = 16 ones (K M^2 = N M shrinks with M).
-    int switch_sweep = (sizeof(Real) == 8 && B == 32) ? late_b16_sweep() : -1;
+    int switch_sweep = (sizeof(Real) == 8 && B == 32) ? kLateB16Sweep : -1;
     MPJ_TRY((configure_twosided<Real, 16>()));
     if (B == 32) MPJ_TRY((configure_twosided<Real, 32>()));
 
@@ -242,7 +233,7 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
     // orthogonal to working precision without it.
     const Real gate = (Real)(dbl ? 1.0 / 64.0 : 1.0 / 4096.0);
     // double-float tile products when both block rotations have max |F| <= 2^-8
-    const float df_gate = dbl ? df_gate_override(1.0f / 256.0f) : -1.0f;
+    const float df_gate = dbl ? kDfGate : -1.0f;
     while (res->sweeps < max_sweeps) {
         if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }

@@ -8,6 +8,8 @@ The oracle runs at sizes it finishes in seconds (several 64-wide tiles plus a
 ragged tail); the full-size cases are checked through properties that hold at
 any size (residual, orthogonality, the constructed spectrum).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -352,3 +354,129 @@ def test_mgs_block_tensor_core_parity(mpj):
     Qg = host(mpj.mgs(dev(Z)))
     assert np.abs(Qg - Qo).max() <= 10 * n * U * kappa
     assert np.linalg.norm(Qg.T @ Qg - np.eye(n)) <= 10 * n * U
+
+
+# ------------------------------------------------------------------ stored oracle results (n = 512, 1024)
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def oracle_fixture(name):
+    """Eigenvalues the oracle computed for a seeded input (tests/golden/
+    make_oracle_fixtures.py, which calls only oracle/ and the input generators)."""
+    vals = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            if not line.startswith("#"):
+                vals.extend(float(v) for v in line.split())
+    return np.array(vals)
+
+
+@pytest.mark.parametrize("kind", ["uniform", "geometric", "cluster"])
+@pytest.mark.parametrize("method", ["mp", "plain"])
+def test_syevj_parity_n1024(mpj, kind, method):
+    """n = 1024 (b = 32, tensor-core FP64 sweeps, 8 slabs of 128 rows) against the
+    oracle's plain Jacobi eigenvalues of the same seeded matrix."""
+    n = 1024
+    A, lam = synth.sym_matrix(n, kind, seed=synth.seed_for(1, n))
+    Lo = oracle_fixture(f"oracle_eig_n1024_{kind}.txt")
+    f = mpj.syevj_mp if method == "mp" else mpj.syevj_plain
+    Lg, Vg, st = f(dev(A))
+    Lg, Vg = host(Lg), host(Vg)
+    a2 = np.abs(lam).max()
+    assert np.abs(Lg - Lo).max() <= 10 * n * U * a2
+    res, orth = evd_metrics(A, Lg, Vg)
+    assert res <= 10 * n * U and orth <= 10 * n * U, (res, orth)
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5])
+def test_syevj_multiple_eigenvalues_vs_oracle(mpj, mode):
+    """Example 2 stand-in (r, s) = (4, 128), n = 512: both methods against the
+    oracle's eigenvalues of the same matrix (not only the constructed spectrum)."""
+    n = 512
+    A, lam = synth.sym_matrix_multiple(4, 128, mode, kappa=1e4, seed=synth.seed_for(4, mode))
+    Lo = oracle_fixture(f"oracle_eig_n512_multiple_mode{mode}.txt")
+    for f in (mpj.syevj_mp, mpj.syevj_plain):
+        L, V, st = f(dev(A))
+        assert np.abs(host(L) - Lo).max() <= 10 * n * U * np.abs(lam).max(), f.__name__
+
+
+@pytest.mark.parametrize("n", [257, 1024])
+def test_stage1_tensor_core_parity(mpj, n):
+    """Step 1 on the tensor-core FP32 engine (b = 32): the FP32 eigenvalues against
+    the oracle's single precision Jacobi (oracle.stage1_syev_f) within 10 n upsilon
+    ||A||_2, init-Res and orthogonality of Z within 10 n upsilon (Table 6.2)."""
+    A, lam = synth.sym_matrix(n, "uniform", seed=500 + n)
+    if n <= 300:
+        _, Do, _ = oracle.stage1_syev_f(A)
+    else:
+        Do = oracle_fixture(f"oracle_stage1_n{n}_uniform.txt")
+    Z, D, st = mpj.stage1_syevj32(dev(A))
+    Z, D = host(Z), host(D)
+    a2 = np.abs(lam).max()
+    assert np.abs(D - Do).max() <= 10 * n * UPS * a2
+    assert np.linalg.norm(A @ Z - Z * D) / np.linalg.norm(A) <= 10 * n * UPS
+    assert np.linalg.norm(Z.T @ Z - np.eye(n)) <= 10 * n * UPS
+
+
+@pytest.mark.parametrize("n", [257, 1024])
+def test_syevj_mp_one_term_tf32_stage1(mpj, n):
+    """A lower-precision step 1 (TF32 hi*hi products only, about 2^-11; Sec. 6,
+    Figs. 6.2-6.3): the FP64 sweeps still reach the FP64 bars against the oracle,
+    with at least as many FP64 sweeps as the three-term step 1."""
+    kind = "uniform"
+    A, lam = synth.sym_matrix(n, kind, seed=synth.seed_for(1, n))
+    Lo = oracle.syevj_plain(A)[0] if n <= 300 else oracle_fixture(f"oracle_eig_n{n}_{kind}.txt")
+    L1, V1, st1 = mpj.syevj_mp(dev(A), options={"stage1_tf32_terms": 1, "tol_stage1": 2.0 ** -10})
+    L3, V3, st3 = mpj.syevj_mp(dev(A))
+    L1, V1 = host(L1), host(V1)
+    a2 = np.abs(lam).max()
+    assert np.abs(L1 - Lo).max() <= 10 * n * U * a2
+    res, orth = evd_metrics(A, L1, V1)
+    assert res <= 10 * n * U and orth <= 10 * n * U, (res, orth)
+    assert st1["sweeps"] >= st3["sweeps"]
+    assert st1["off_T0"] > st3["off_T0"]
+
+
+@pytest.mark.parametrize("kind", ["uniform", "geometric", "cluster"])
+@pytest.mark.parametrize("method", ["mp", "plain"])
+def test_syevj_parity_simt_engines(mpj, kind, method):
+    """The SIMT engines kept for comparison (MPJ_OPT_SIMT_STAGE1 / SIMT_SWEEPS /
+    FP64_PRODUCTS: double-float and FP64 tile products, FP64 GEMMs) at b = 32
+    against the oracle."""
+    n = 257
+    A, lam = synth.sym_matrix(n, kind, seed=synth.seed_for(1, n))
+    Lo, Vo, sto, rco = oracle.syevj_plain(A)
+    flags = mpj.OPT_SIMT_STAGE1 | mpj.OPT_SIMT_SWEEPS | mpj.OPT_FP64_PRODUCTS
+    f = mpj.syevj_mp if method == "mp" else mpj.syevj_plain
+    Lg, Vg, st = f(dev(A), options={"flags": flags})
+    Lg, Vg = host(Lg), host(Vg)
+    assert np.abs(Lg - Lo).max() <= 10 * n * U * np.abs(lam).max()
+    res, orth = evd_metrics(A, Lg, Vg)
+    assert res <= 10 * n * U and orth <= 10 * n * U
+
+
+def test_syevj_mp_full_inner_schedule(mpj):
+    """The full-tournament inner schedule of the tensor-core FP64 sweeps
+    (MPJ_OPT_FULL_INNER) against the oracle."""
+    n = 513
+    A, lam = synth.sym_matrix(n, "cluster", seed=synth.seed_for(1, n))
+    Lo = oracle.syevj_plain(A)[0]
+    Lg, Vg, st = mpj.syevj_mp(dev(A), options={"flags": mpj.OPT_FULL_INNER})
+    Lg, Vg = host(Lg), host(Vg)
+    assert np.abs(Lg - Lo).max() <= 10 * n * U * np.abs(lam).max()
+    res, orth = evd_metrics(A, Lg, Vg)
+    assert res <= 10 * n * U and orth <= 10 * n * U
+
+
+def test_congruence_parity_n1024(mpj):
+    """Step 3 at n = 1024 elementwise against oracle.congruence (extended
+    precision) within the FP64 bound of Sec. 4."""
+    n = 1024
+    A, _ = synth.sym_matrix(n, "uniform", seed=200 + n)
+    Q = synth.haar(synth.rng_for(300 + n), n)
+    To = oracle.congruence(A, Q)
+    Tg = host(mpj.congruence(dev(A), dev(Q)))
+    assert np.array_equal(Tg, Tg.T)
+    gn = n * U / (1 - n * U)
+    bound = gn * (2 + gn) * (np.abs(Q).T @ np.abs(A) @ np.abs(Q))
+    assert (np.abs(Tg - To) <= 2 * bound).all()

@@ -103,3 +103,31 @@ def test_alg_counts_closed_forms(n):
     assert realised["apply2_f64"] == 2 * 4.0 * Np ** 3
     # one FP32 matrix read and written per pass and round
     assert c["tc1_f32"] == 8.0 * Np * Np * (Np // 32 - 1) * 11
+
+
+def test_library_reads_no_environment():
+    """Every switch of the numerical path is an mpj_options field: the library's
+    sources call no getenv, so a default C-ABI call cannot change path with the
+    caller's environment."""
+    import glob
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                        "paper_2211_03339_gb300", "csrc")
+    files = glob.glob(os.path.join(root, "*.cu")) + glob.glob(os.path.join(root, "*.cuh")) + \
+        glob.glob(os.path.join(root, "*.h"))
+    assert files
+    for f in files:
+        assert "getenv" not in open(f).read(), f
+
+
+def test_options_mirror_matches_header():
+    """The Python mirror of mpj_options has the header's fields in the header's
+    order, and the OPT_* constants have the header's values."""
+    import re
+    import paper_2211_03339_gb300 as m
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "mpjacobi.h")).read()
+    body = hdr[hdr.index("typedef struct mpj_options {"):hdr.index("} mpj_options;")]
+    fields = re.findall(r"^\s+(?:int|double)\s+(\w+);", body, re.M)
+    assert fields == [f for f, _ in m.Options._fields_]
+    for name, val in re.findall(r"#define MPJ_(OPT_\w+)\s+(\d+)", hdr):
+        assert getattr(m, name) == int(val), name

@@ -413,3 +413,25 @@ def test_svd_constructed(mp):
     assert np.abs(S - np.linalg.svd(A, compute_uv=False)).max() <= 10 * n * U * sig[0]
     if mp:
         assert st["sweeps"] <= 6
+
+
+def test_stage1_gesvj_f_alone():
+    """Step 1 of Alg. 5.2 in the oracle, pinned on its own: Z orthogonal to the
+    single precision level, its columns ordered by decreasing ||fl32(A) z_j||, and
+    each z_j the right singular vector LAPACK gives for sigma_j, up to sign and to
+    the single precision accuracy that the gap to the neighbouring singular values
+    allows (a transposed Z or a wrong column order fails these)."""
+    m, n = 60, 24
+    A, sig, _, _ = synth.svd_matrix(m, n, seed=31, sigma_min=1e-2)
+    Z, st = oracle.stage1_gesvj_f(A)
+    assert st["sweeps_stage1"] >= 1
+    assert np.linalg.norm(Z.T @ Z - np.eye(n)) <= 10 * n * UPS
+    A32 = A.astype(np.float32).astype(np.float64)
+    norms = np.linalg.norm(A32 @ Z, axis=0)
+    assert (np.diff(norms) <= 4 * UPS * norms[0]).all()
+    _, s, Vt = np.linalg.svd(A)
+    gaps = np.minimum(np.abs(np.diff(s, prepend=np.inf)), np.abs(np.diff(s, append=-np.inf)))
+    for j in range(n):
+        v = Vt[j]
+        zj = Z[:, j] * np.sign(Z[:, j] @ v)
+        assert np.abs(zj - v).max() <= 100 * UPS * s[0] / gaps[j], j
