@@ -289,6 +289,8 @@ struct SvdBufs {
     float *C32, *V32;
     void* eng;
     void* mgsw;
+    void *ozA, *ozQ, *ozs;       // tensor-core operand slices (mp only): rows of A, Q, MGS panels
+    double* Rbuf;                // 256 x n projections of the block MGS (mp only)
     double* nrm;
     Scal sc;
 };
@@ -303,9 +305,14 @@ int svd_layout(Arena& a, int m, int n, int N, int B, bool mp, SvdBufs& b) {
     b.eng = a.take<char>(max2(onesided_workspace_bytes<double>(m, N, B),
                               onesided_workspace_bytes<float>(m, N, B)));
     b.mgsw = mp ? a.take<char>(mgs_workspace_bytes(n, n)) : nullptr;
+    b.ozA = mp ? a.take<char>(oz_operand_bytes(m, n)) : nullptr;
+    b.ozQ = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
+    b.ozs = mp ? a.take<char>(mgs_panel_oz_bytes(n, n)) : nullptr;
+    b.Rbuf = mp ? a.take<double>(256 * (size_t)n) : nullptr;
     b.nrm = a.take<double>((size_t)N);
     MPJ_TRY(take_scal(a, n, b.sc));
-    if (a.base && (!b.C64 || !b.V64 || !b.eng || !b.nrm || (mp && (!b.Q || !b.C32 || !b.V32 || !b.mgsw))))
+    if (a.base && (!b.C64 || !b.V64 || !b.eng || !b.nrm ||
+                   (mp && (!b.Q || !b.C32 || !b.V32 || !b.mgsw || !b.ozA || !b.ozQ || !b.ozs || !b.Rbuf))))
         return MPJ_BAD_ARG;
     return MPJ_SUCCESS;
 }
@@ -359,10 +366,24 @@ int gesvj_impl(bool mp, const double* A, int m, int n, int lda, double* Sigma, d
         MPJ_TRY(rank_sort(b.sc.d, 1, n, true, b.sc.perm, s));
         MPJ_TRY(gather_z32(b.V32, N, b.sc.perm, n, b.Q, n, s));
         tm.mark(1);
-        MPJ_TRY(mgs_inplace(b.Q, n, n, n, b.mgsw, b.sc.flag, s));                          // step 2
+        if (n >= 1024 && oz_enabled() && oz_supported(n, n, n)) {                           // step 2
+            MPJ_TRY(mgs_blocked_oz(b.Q, n, n, n, b.mgsw, b.sc.flag, b.ozA, b.ozs, b.Rbuf, s));
+        } else {
+            MPJ_TRY(mgs_inplace(b.Q, n, n, n, b.mgsw, b.sc.flag, s));
+        }
         tm.mark(2);
         MPJ_CUDA_TRY(cudaMemsetAsync(b.C64, 0, sizeof(double) * (size_t)m * N, s));        // step 3
-        MPJ_TRY(dgemm(false, false, m, n, n, 1.0, A, lda, b.Q, n, 0.0, b.C64, m, false, s));
+        if (oz_enabled() && oz_supported(m, n, n)) {
+            // C = A Q on the tensor cores by exact splitting: rows of A, columns of Q
+            OzOperand oa, oq;
+            MPJ_TRY(oz_operand(b.ozA, m, n, &oa));
+            MPJ_TRY(oz_operand(b.ozQ, n, n, &oq));
+            MPJ_TRY(oz_slice(A, 1, lda, m, n, &oa, s));
+            MPJ_TRY(oz_slice(b.Q, n, 1, n, n, &oq, s));
+            MPJ_TRY(oz_gemm(oa, oq, 1.0, 0.0, b.C64, m, false, b.sc.flag, s));
+        } else {
+            MPJ_TRY(dgemm(false, false, m, n, n, 1.0, A, lda, b.Q, n, 0.0, b.C64, m, false, s));
+        }
         MPJ_TRY(copy_pad_f64(b.Q, n, n, n, b.V64, N, N, N, true, s));                      // V = Q
         tm.mark(3);
         int fl = 0;

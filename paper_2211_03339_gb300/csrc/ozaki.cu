@@ -5,11 +5,12 @@
 //
 // Each row i of op(A) is scaled by 2^(7 - e_i) (e_i the binary exponent of the
 // row's largest |entry|, so the scaled row lies in (-128, 128)) and cut into
-// S = 8 integer slices of 7 bits: a = sum_s a_s 2^(-7 s), a_0 in [-128, 128],
-// a_s in [-64, 64] (round to nearest at each step).  Eight slices reach down to
-// 2^-49 of the scaled row, i.e. 2^-56 of 2^e_i: every entry within 2^3 of the
-// row maximum is cut exactly.  Columns of op(B) likewise.  Integers of magnitude
-// <= 128 are exact in bf16, their products exact in FP32, and
+// S = 8 balanced integer slices of 7 bits from the FP64 bit patterns with
+// integer operations (slice_device.cuh): a = sum_s a_s 2^(-7 s), |a_0| <= 128,
+// a_s in [-64, 63].  Eight slices reach down to 2^-49 of the scaled row, i.e.
+// 2^-56 of 2^e_i: every entry within 2^3 of the row maximum is cut exactly.
+// Columns of op(B) likewise.  Integers of magnitude <= 128 are exact in bf16,
+// their products exact in FP32, and
 //
 //   C_ij = 2^(e_i + f_j - 14) sum_d 2^(-7 d) T_d(i, j),
 //   T_d  = sum_{s + t = d} sum_k a_s(i, k) b_t(k, j),     d = 0 .. 7,
@@ -28,8 +29,9 @@
 //
 // Kernel: one CTA per 128 x 32 tile of C; warp 4 streams the 8 + 8 slice planes
 // of each K step of 32 with TMA (3-D boxes, 64-byte swizzle) into a 2-stage
-// ring, warp 5 issues the 36 x 2 MMAs of a K step into eight 32-column TMEM
-// accumulators, warps 0-3 drain each K block into the int32 totals and finally
+// ring, warp 5 issues the slice products of a K step into eight 32-column TMEM
+// accumulators (one MMA per A plane, its N spanning the B planes of all its
+// levels), warps 0-3 drain each K block into the int32 totals and finally
 // write C.
 #include <cmath>
 #include <cstdint>
@@ -39,6 +41,7 @@
 
 #include "internal.h"
 #include "tc_device.cuh"
+#include "slice_device.cuh"
 
 namespace mpj {
 
@@ -61,33 +64,43 @@ struct OzMaps {
 };
 
 // --------------------------------------------------------------- slicing
-__device__ __forceinline__ void slice_store(double a, __nv_bfloat16* P, size_t pstride, size_t off) {
+// The row exponent e_i is kept in frexp form (max |row| in [2^(e_i - 1), 2^e_i)):
+// e_i = E_r - 1022 for the row's exponent class E_r.
+
+// 8 consecutive entries of one row, sliced against class Er, as one 16-byte
+// chunk per plane at P + p pstride.
+__device__ __forceinline__ void slice8_store(const double (&x)[8], int Er, __nv_bfloat16* P, size_t pstride) {
+    uint64_t v[8];
 #pragma unroll
-    for (int p = 0; p < kS; ++p) {
-        const double s = rint(a);
-        P[p * pstride + off] = __float2bfloat16_rn((float)s);
-        a = (a - s) * 128.0;
-    }
+    for (int e = 0; e < 8; ++e) v[e] = slice::scaled_signed(x[e], Er);
+#pragma unroll
+    for (int p = 0; p < kS; ++p)
+        *reinterpret_cast<uint4*>(P + p * pstride) =
+            make_uint4(slice::digit_pair(v[0], v[1], p), slice::digit_pair(v[2], v[3], p),
+                       slice::digit_pair(v[4], v[5], p), slice::digit_pair(v[6], v[7], p));
 }
 
-// Rows contiguous: row r is X[r * rs + k], k < K.  One CTA (128 threads) per row.
+// Rows contiguous: row r is X[r * rs + k], k < K.  One CTA (128 threads) per row;
+// each thread slices 8 consecutive entries at a time.
 __global__ void __launch_bounds__(128)
 k_oz_slice_rows(const double* __restrict__ X, long long rs, int rows, int K, int Kp,
                 __nv_bfloat16* __restrict__ P, long long pstride, int* __restrict__ ex) {
-    __shared__ double red[4];
+    __shared__ int red[4];
     const int r = blockIdx.x;
     const double* x = X + (size_t)r * rs;
-    double m = 0.0;
-    for (int k = threadIdx.x; k < K; k += 128) m = fmax(m, fabs(x[k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    int cls = 0;
+    for (int k = threadIdx.x; k < K; k += 128) cls = max(cls, slice::exp_class(x[k]));
+    for (int o = 16; o > 0; o >>= 1) cls = max(cls, __shfl_xor_sync(0xffffffffu, cls, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = cls;
     __syncthreads();
-    m = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
-    int e = 0;
-    if (m > 0.0 && m <= 1.7976931348623157e308) frexp(m, &e);   // m 2^-e in [0.5, 1)
-    if (threadIdx.x == 0) ex[r] = e;
-    for (int k = threadIdx.x; k < Kp; k += 128)
-        slice_store(k < K ? ldexp(x[k], 7 - e) : 0.0, P, (size_t)pstride, (size_t)r * Kp + k);
+    cls = max(max(red[0], red[1]), max(red[2], red[3]));
+    if (threadIdx.x == 0) ex[r] = cls - 1022;
+    for (int k0 = 8 * threadIdx.x; k0 < Kp; k0 += 8 * 128) {
+        double xv[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) xv[e] = k0 + e < K ? x[k0 + e] : 0.0;
+        slice8_store(xv, cls, P + (size_t)r * Kp + k0, (size_t)pstride);
+    }
 }
 
 // Rows of a column-major matrix (row r is X[r + k * ks]), in two passes: the row
@@ -98,11 +111,9 @@ __global__ void __launch_bounds__(128)
 k_oz_rowexp_strided(const double* __restrict__ X, long long ks, int rows, int K, int* __restrict__ ex) {
     const int r = blockIdx.x * 128 + threadIdx.x;
     if (r >= rows) return;
-    double m = 0.0;
-    for (int k = 0; k < K; ++k) m = fmax(m, fabs(X[(size_t)r + (size_t)k * ks]));
-    int e = 0;
-    if (m > 0.0 && m <= 1.7976931348623157e308) frexp(m, &e);
-    ex[r] = e;
+    int cls = 0;
+    for (int k = 0; k < K; ++k) cls = max(cls, slice::exp_class(X[(size_t)r + (size_t)k * ks]));
+    ex[r] = cls - 1022;
 }
 
 __global__ void __launch_bounds__(256)
@@ -119,26 +130,12 @@ k_oz_slice_tiled(const double* __restrict__ X, long long ks, int rows, int K, in
     __syncthreads();
     const int rr = tid / 8, kg = (tid % 8) * 8;              // 8 consecutive k per thread
     const int r = r0 + rr;
-    if (r >= rows) return;
-    const int e = ex[r];
-    __nv_bfloat16 out[kS][8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        double a = ldexp(tile[kg + j][rr], 7 - e);
-#pragma unroll
-        for (int p = 0; p < kS; ++p) {
-            const double sl = rint(a);
-            out[p][j] = __float2bfloat16_rn((float)sl);
-            a = (a - sl) * 128.0;
-        }
-    }
     const int kb = k0 + kg;
-    if (kb + 8 <= Kp) {
+    if (r >= rows || kb + 8 > Kp) return;
+    double xv[8];
 #pragma unroll
-        for (int p = 0; p < kS; ++p)
-            *reinterpret_cast<uint4*>(P + p * (size_t)pstride + (size_t)r * Kp + kb) =
-                *reinterpret_cast<const uint4*>(out[p]);
-    }
+    for (int j = 0; j < 8; ++j) xv[j] = tile[kg + j][rr];
+    slice8_store(xv, ex[r] + 1022, P + (size_t)r * Kp + kb, (size_t)pstride);
 }
 
 // --------------------------------------------------------------- product
@@ -235,7 +232,6 @@ k_oz_gemm(const __grid_constant__ OzMaps maps, const int* __restrict__ exA, cons
         }
     } else if (warp == 5) {
         if (lane == 0) {                                   // MMA issuer
-            constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, kTM, kTN);
             bool ok = true;
             for (int kb = 0; kb < nkb && ok; ++kb) {
                 if (kb > 0) {
@@ -251,17 +247,19 @@ k_oz_gemm(const __grid_constant__ OzMaps maps, const int* __restrict__ exA, cons
                     tc::fence_after_sync();
                     const uint32_t a0 = tc::smem_u32(sm + (size_t)slot * kStageBytes);
                     const uint32_t b0 = a0 + kS * kAPlane;
+                    // The 8 B planes of the stage lie one after another (32 rows each,
+                    // 512-byte row groups throughout): one K-major operand of 256 rows.
+                    // Level s + t sits at TMEM column 32 (s + t), so the products of A
+                    // plane s with B planes 0 .. 7 - s are one MMA with N = 32 (8 - s)
+                    // and D at column 32 s (8 MMAs per K step of 16 instead of 36).
 #pragma unroll
                     for (int ks = 0; ks < kKS / 16; ++ks) {
 #pragma unroll
-                        for (int d = 0; d < kS; ++d) {
-#pragma unroll
-                            for (int s = 0; s <= d; ++s) {
-                                const int t = d - s;
-                                const uint32_t acc = (st == 0 && ks == 0 && s == 0) ? 0u : 1u;
-                                tc::mma_f16(tmem + d * kTN, desc_sw64(a0 + s * kAPlane + ks * 32),
-                                            desc_sw64(b0 + t * kBPlane + ks * 32), idesc, acc);
-                            }
+                        for (int s = 0; s < kS; ++s) {
+                            const uint32_t acc = (st == 0 && ks == 0 && s == 0) ? 0u : 1u;
+                            tc::mma_f16(tmem + s * kTN, desc_sw64(a0 + s * kAPlane + ks * 32),
+                                        desc_sw64(b0 + ks * 32), tc::instr_desc(tc::kFmtBF16, kTM, kTN * (kS - s)),
+                                        acc);
                         }
                     }
                     tc::commit(&empty[slot]);                // the stage is free once these complete

@@ -45,8 +45,11 @@
 #include "internal.h"
 #include "engine_device.cuh"
 #include "tc_device.cuh"
+#include "slice_device.cuh"
 
 namespace mpj {
+
+using namespace slice;
 
 namespace {
 
@@ -65,51 +68,6 @@ constexpr int kOffA = 2 * kXBytes;           // two A plane slots
 constexpr int kOffB = kOffA + 2 * kAPlane;   // the 8 B planes and column exponents
 constexpr int kOffE = kOffB + kS * kBPlane;   // column exponents, one copy per X stage
 constexpr size_t kPassSmem = (size_t)kOffE + 2 * 256 + 1024;
-// 64 at each of the seven lower 7-bit digit positions and 256 at the top one:
-// for a signed M_s (|M_s| < 2^56), M_s + kBias is positive and below 2^58; its
-// base-128 digits (the top one 9 bits wide) minus 64 (minus 256 at the top) are
-// the balanced digits of M_s, M_s = sum_s d_s 2^(49 - 7 s), |d_0| <= 128,
-// d_s in [-64, 63].
-constexpr uint64_t kBias =
-    64ull * ((1ull << 42) + (1ull << 35) + (1ull << 28) + (1ull << 21) + (1ull << 14) + (1ull << 7) + 1ull) +
-    (1ull << 57);
-
-// ---------------------------------------------------------------- slicing
-// Exponent class of x for a row maximum: 0 for x == 0, else max(E, 1) with E the
-// biased exponent (subnormals count as 1).  Integer operations only.
-__device__ __forceinline__ int exp_class(double x) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
-    const int E = (hi >> 20) & 0x7FF;
-    const int nz = ((hi & 0xFFFFFu) | lo) != 0u;
-    return E ? E : nz;
-}
-
-// M_s + kBias for M_s = sign(x) trunc(|x| 2^(1078 - Er)), Er >= exp_class(x).
-__device__ __forceinline__ uint64_t scaled_signed(double x, int Er) {
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const int E = (int)((b >> 52) & 0x7FF);
-    uint64_t mant = b & 0xFFFFFFFFFFFFFull;
-    if (E) mant |= 1ull << 52;
-    const int sh = (E ? E : 1) - Er + 3;          // <= 3
-    const uint64_t M = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> -sh) : 0ull);
-    const uint64_t sm = (uint64_t)((long long)b >> 63);   // all ones for a negative x
-    return ((M ^ sm) - sm) + kBias;
-}
-
-// Digit s of a biased value as an exact float: the raw field (9 bits at the top
-// digit, 7 below) through the magic constant 2^23, minus 2^23 and the bias.
-__device__ __forceinline__ float digit_f(uint64_t v, int s) {
-    const uint32_t r = (uint32_t)(v >> (49 - 7 * s)) & (s == 0 ? 0x1FFu : 0x7Fu);
-    return __fsub_rn(__uint_as_float(0x4B000000u | r), s == 0 ? 8388864.0f : 8388672.0f);
-}
-
-// bf16 pair of digit s of two elements (e0 in the low half): the floats are
-// small integers, so their upper halves are exact bf16.
-__device__ __forceinline__ uint32_t digit_pair(uint64_t v0, uint64_t v1, int s) {
-    return __byte_perm(__float_as_uint(digit_f(v0, s)), __float_as_uint(digit_f(v1, s)), 0x7632);
-}
-
 // Byte offset of 16-byte chunk j (elements 8j..8j+7 along K) of row r in a
 // K-major operand of 128-byte rows with the 128-byte swizzle.
 __device__ __forceinline__ int sw_chunk(int r, int j) {
@@ -262,26 +220,26 @@ __device__ __forceinline__ bool bar_or(int id, int count, bool p) {
     return r != 0;
 }
 
-// Wait for phase `parity` of an mbarrier, suspending the thread in the
-// barrier unit between polls (suspend-time hint 20 us) instead of spinning.
-__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, int polls) {
+// Wait for phase `parity` of an mbarrier: try_wait polls, each of which may
+// suspend the thread for a short, system-defined time.
+__device__ __forceinline__ bool mbar_poll(uint64_t* bar, uint32_t parity, int polls) {
     uint32_t done = 0;
     for (int it = 0; it < polls && !done; ++it) {
         asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             "selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(tc::smem_u32(bar)), "r"(parity), "r"(20000u)
+            : "r"(tc::smem_u32(bar)), "r"(parity)
             : "memory");
     }
     return done != 0;
 }
 
-// Bounded wait (about two seconds at most) that gives up early once another
-// role has recorded a failure.
+// Bounded wait (a few million polls, seconds at most) that gives up early once
+// another role has recorded a failure.
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, volatile int* failed) {
-    for (int r = 0; r < 100; ++r) {
-        if (mbar_wait_sleep(bar, parity, 1000)) return true;
+    for (int r = 0; r < 256; ++r) {
+        if (mbar_poll(bar, parity, 16384)) return true;
         if (*failed) return false;
     }
     *failed = 1;
@@ -300,7 +258,10 @@ __device__ __forceinline__ bool item_taken(int it, int n_slabs, int skip_identit
 //   warp 0     producer: TMA loads of the FP64 tiles into a 2-stage ring, and
 //              the digit planes of F_b (one bulk copy) when the pair changes;
 //   warp 1     MMA issuer (one thread): for each digit plane s of the tile the
-//              products (s, t), t <= 7 - s, into the level accumulators s + t;
+//              products (s, t), t <= 7 - s, into the level accumulators s + t, as
+//              MMAs with N = 64 g over groups of g <= 4 consecutive B planes (12
+//              MMAs per K step of 16; a single thread issuing 36 MMAs of N = 64
+//              per K step was the tile's bottleneck);
 //   warps 2-9  slicers: per tile row, the row exponent class, then the 8 digit
 //              planes one by one into a 2-slot ring;
 //   warps 10-17 epilogue: the levels of its 32 columns folded into 64-bit
@@ -380,8 +341,10 @@ k_pass_tc64(const __grid_constant__ Tc64Maps maps, int N, int n_slabs, int total
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t idesc = tc::instr_desc(tc::kFmtBF16, kSlab, kM);
-            const uint32_t b0 = tc::smem_u32(Bp);
+            // descriptors of the slot and plane bases; a K step or another plane only
+            // moves the start-address field (address / 16, no carry: smem < 256 KB)
+            const uint64_t adesc0 = tc::smem_desc_sw128(tc::smem_u32(Ap));
+            const uint64_t bdesc0 = tc::smem_desc_sw128(tc::smem_u32(Bp));
             int k = 0;
             uint32_t q = 0;
             bool ok = true;
@@ -394,13 +357,22 @@ k_pass_tc64(const __grid_constant__ Tc64Maps maps, int N, int n_slabs, int total
                     const int slot = q & 1;
                     if (!wait_or_fail(&afull[slot], (q >> 1) & 1, &failed)) { ok = false; break; }
                     tc::fence_after_sync();
-                    const uint32_t a0 = tc::smem_u32(Ap + slot * kAPlane);
-                    for (int t = 0; t + sa < kS; ++t)
+                    const uint64_t ad = adesc0 + (uint64_t)(slot * (kAPlane >> 4));
+                    // The 8 B planes lie one after another (64 rows each, 1024-byte row
+                    // groups throughout), i.e. they form one K-major operand of 512 rows,
+                    // and level s + t sits at TMEM column 64 (s + t): the products of this
+                    // A plane with B planes t0 .. t0 + g - 1 are ONE MMA with N = 64 g and
+                    // D at column 64 (s + t0).  Groups of at most 4 planes (N <= 256).
+                    for (int t0 = 0; t0 + sa < kS; t0 += 4) {
+                        const int g = min(4, kS - sa - t0);
+                        const uint32_t idesc = tc::instr_desc(tc::kFmtBF16, kSlab, kM * g);
+                        const uint64_t bd = bdesc0 + (uint64_t)(t0 * (kBPlane >> 4));
+                        const uint32_t dcol = tmem + (uint32_t)((sa + t0) * kM);
 #pragma unroll
                         for (int ks = 0; ks < kM / 16; ++ks)
-                            tc::mma_f16(tmem + (uint32_t)((sa + t) * kM), tc::smem_desc_sw128(a0 + ks * 32),
-                                        tc::smem_desc_sw128(b0 + t * kBPlane + ks * 32), idesc,
+                            tc::mma_f16(dcol, ad + (uint64_t)(ks * 2), bd + (uint64_t)(ks * 2), idesc,
                                         (sa == 0 && ks == 0) ? 0u : 1u);
+                    }
                     tc::commit(&aempty[slot]);
                 }
                 if (!ok) break;

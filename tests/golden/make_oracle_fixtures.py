@@ -1,6 +1,7 @@
 """Write the oracle's results for the GPU parity cases whose oracle run takes
 minutes (n = 512 and 1024): the plain FP64 Jacobi eigenvalues (Algorithm 3.2,
-oracle.syevj_plain) and the FP32 step-1 eigenvalues (oracle.stage1_syev_f).
+oracle.syevj_plain), the FP32 step-1 eigenvalues (oracle.stage1_syev_f) and the
+singular values of the one-sided Jacobi SVD (Algorithm 5.1, oracle.gesvj_plain).
 
 Only oracle/ and the seeded input generators (paper_2211_03339_gb300.synth, no
 arithmetic of the method) are called; nothing comes from the CUDA path.  The
@@ -22,6 +23,8 @@ CASES = [("oracle_eig_n1024_%s.txt" % k, "eig", ("sym", 1024, k, 1000 + 1024)) f
 CASES += [("oracle_stage1_n1024_uniform.txt", "stage1", ("sym", 1024, "uniform", 500 + 1024))]
 CASES += [("oracle_eig_n512_multiple_mode%d.txt" % m, "eig", ("multiple", 4, 128, m, 1e4, 4000 + m))
           for m in (1, 2, 3, 4, 5)]
+CASES += [("oracle_svd_1300x1100.txt", "svd", ("svd", 1300, 1100, 1e-10, 2000 + 1100))]
+ONLY = sys.argv[1:]        # optional file names: write only these
 
 
 def make_input(spec):
@@ -29,6 +32,9 @@ def make_input(spec):
     if spec[0] == "sym":
         _, n, kind, seed = spec
         return synth.sym_matrix(n, kind, seed=seed)[0]
+    if spec[0] == "svd":
+        _, m, n, smin, seed = spec
+        return synth.svd_matrix(m, n, seed=seed, sigma_min=smin)[0]
     _, r, s, mode, kappa, seed = spec
     return synth.sym_matrix_multiple(r, s, mode, kappa=kappa, seed=seed)[0]
 
@@ -43,6 +49,11 @@ def run(case):
         assert rc == 0
         vals = np.asarray(L)
         head = "# oracle.syevj_plain eigenvalues (ascending), %s, sweeps %d" % (spec, st["sweeps"])
+    elif what == "svd":
+        S, Uo, Vo, st, rc = oracle.gesvj_plain(A)
+        assert rc == 0
+        vals = np.asarray(S)
+        head = "# oracle.gesvj_plain singular values (descending), %s, sweeps %d" % (spec, st["sweeps"])
     else:
         Z, D, st = oracle.stage1_syev_f(A)
         vals = np.asarray(D)
@@ -58,5 +69,6 @@ if __name__ == "__main__":
     import oracle
     oracle.build()
     with mp.get_context("spawn").Pool(min(len(CASES), os.cpu_count() or 1)) as pool:
-        for name in pool.imap_unordered(run, CASES):
+        cases = [c for c in CASES if not ONLY or c[0] in ONLY]
+        for name in pool.imap_unordered(run, cases):
             print("wrote", name, flush=True)

@@ -480,3 +480,20 @@ def test_congruence_parity_n1024(mpj):
     gn = n * U / (1 - n * U)
     bound = gn * (2 + gn) * (np.abs(Q).T @ np.abs(A) @ np.abs(Q))
     assert (np.abs(Tg - To) <= 2 * bound).all()
+
+
+@pytest.mark.parametrize("method", ["mp", "plain"])
+def test_gesvj_parity_1300x1100(mpj, method):
+    """SVD at n >= 1024: the block MGS with tensor-core panel projections (step 2)
+    and C = A Q by exact splitting (step 3) on the preconditioned path; singular
+    values against the oracle's one-sided Jacobi of the same matrix."""
+    m, n = 1300, 1100
+    A, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, n), sigma_min=1e-10)
+    So = oracle_fixture("oracle_svd_1300x1100.txt")
+    f = mpj.gesvj_mp if method == "mp" else mpj.gesvj_plain
+    Sg, Ug, Vg, st = f(dev(A), options={"max_sweeps": 100})
+    Sg, Ug, Vg = host(Sg), host(Ug), host(Vg)
+    assert np.abs(Sg - So).max() <= 10 * n * U * sig[0]
+    assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
+    assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
+    assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
