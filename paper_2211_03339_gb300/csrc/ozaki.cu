@@ -282,7 +282,8 @@ k_oz_gemm(const __grid_constant__ OzMaps maps, const int* __restrict__ exA, cons
                     tc::tmem_wait_ld();
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
-                        const int v = __float2int_rn(__uint_as_float(f[j]));
+                        // |f| < 2^22: f + 1.5 2^23 has the bit pattern 0x4B400000 + f
+                        const int v = (int)__float_as_uint(__fadd_rn(__uint_as_float(f[j]), 12582912.0f)) - 0x4B400000;
                         t[j] = kb > 0 ? (uint32_t)((int)t[j] + v) : (uint32_t)v;
                     }
                     tmem_st32(lanebase + kAccCols + d * kTN, t);
@@ -293,27 +294,44 @@ k_oz_gemm(const __grid_constant__ OzMaps maps, const int* __restrict__ exA, cons
             named_bar_drain();
             if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&accempty)) : "memory");
         }
-        // epilogue: C_ij = alpha 2^(e_i + f_j - 14) sum_d 2^(-7 d) T_d + beta C_ij
+        // epilogue: C_ij = alpha 2^(e_i + f_j - 14) sum_d 2^(-7 d) T_d + beta C_ij.  The
+        // levels are summed exactly as two integers, S_hi = sum_{d<4} T_d 2^(7 (3 - d))
+        // and S_lo = sum_{d>=4} T_d 2^(7 (7 - d)) (|T_d| < 2^30: both below 2^52, exact
+        // in FP64), so that sum_d 2^(-7 d) T_d = 2^-49 (S_hi 2^28 + S_lo) takes two
+        // conversions and one FMA per element.
         const int row = mt * kTM + warp * 32 + lane;
         if (ok && nkb > 0) {
-            double c[32];
-            for (int d = kS - 1; d >= 0; --d) {
-                uint32_t t[32];
-                tmem_ld32(lanebase + kAccCols + d * kTN, t);
-                tc::tmem_wait_ld();
+            const int ea = row < M ? exA[row] : 0;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                long long hi[16], lo[16];
 #pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    c[j] = d == kS - 1 ? (double)(int)t[j] : fma(c[j], 0.0078125, (double)(int)t[j]);
-            }
-            if (row < M) {
-                const int ea = exA[row];
+                for (int j = 0; j < 16; ++j) { hi[j] = 0; lo[j] = 0; }
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = nt * kTN + j;
-                    if (col < N) {
-                        const double v = alpha * ldexp(c[j], ea + exB[col] - 14);
-                        double* cp = C + (size_t)row + (size_t)col * ldc;
-                        *cp = beta != 0.0 ? fma(beta, *cp, v) : v;
+                for (int d = 0; d < kS; ++d) {
+                    float tf[16];
+                    tc::tmem_ld16(lanebase + kAccCols + d * kTN + 16 * h, tf);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const long long tv = (long long)__float_as_int(tf[j]);
+                        if (d < 4) hi[j] = (hi[j] << 7) + tv;
+                        else lo[j] = (lo[j] << 7) + tv;
+                    }
+                }
+                if (row < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = nt * kTN + 16 * h + j;
+                        if (col < N) {
+                            const double sum = fma(__ll2double_rn(hi[j]), 268435456.0, __ll2double_rn(lo[j]));
+                            const int e = ea + exB[col] - 63;
+                            const double v = alpha * (e >= -1022 && e <= 1023
+                                                          ? sum * __longlong_as_double((long long)(e + 1023) << 52)
+                                                          : ldexp(sum, e));
+                            double* cp = C + (size_t)row + (size_t)col * ldc;
+                            *cp = beta != 0.0 ? fma(beta, *cp, v) : v;
+                        }
                     }
                 }
             }

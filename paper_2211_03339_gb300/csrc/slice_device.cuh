@@ -58,10 +58,20 @@ __device__ __forceinline__ float digit_f(uint64_t v, int s) {
     return __fsub_rn(__uint_as_float(0x4B000000u | r), s == 0 ? 8388864.0f : 8388672.0f);
 }
 
-// bf16 pair of digit s of two elements (e0 in the low half): the floats are
-// small integers, so their upper halves are exact bf16.
+// bf16 pair of digit s of two elements (e0 in the low half).  Digit 0: the
+// floats are small integers, so their upper halves are exact bf16.  Digits
+// 1..7: the 7-bit raw fields r are placed in the mantissas of bf16 128 (0x4300
+// | r = 128 + r, exact) and one bf16x2 FMA subtracts 128 + 64, exact since the
+// result r - 64 is a small integer.
 __device__ __forceinline__ uint32_t digit_pair(uint64_t v0, uint64_t v1, int s) {
-    return __byte_perm(__float_as_uint(digit_f(v0, s)), __float_as_uint(digit_f(v1, s)), 0x7632);
+    if (s == 0)
+        return __byte_perm(__float_as_uint(digit_f(v0, 0)), __float_as_uint(digit_f(v1, 0)), 0x7632);
+    const int sh = 49 - 7 * s;
+    const uint32_t r = __byte_perm((uint32_t)(v0 >> sh), (uint32_t)(v1 >> sh), 0x5410);
+    const uint32_t w = (r & 0x007F007Fu) | 0x43004300u;          // bf16x2 (128 + r0, 128 + r1)
+    uint32_t out;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(out) : "r"(w), "r"(0x3F803F80u), "r"(0xC340C340u));
+    return out;                                                    // (r0 - 64, r1 - 64)
 }
 
 }  // namespace slice
