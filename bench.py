@@ -323,6 +323,22 @@ def run_extras(args, dev):
         out[f"syevj_{kind}_n{n}"] = entry
         del A
         torch.cuda.empty_cache()
+    # a lower-precision step 1 (Sec. 6, Figs. 6.2-6.3): three-term TF32 products
+    # (about FP32 accuracy, stop at 2^-21 ||A||_F) against one-term TF32 products
+    # (about 2^-11, stop at 2^-10 ||A||_F), uniform spectrum at n = 4096
+    A_np, lam = synth.sym_matrix(4096, "uniform", seed=synth.seed_for(1, 0))
+    A = torch.from_numpy(A_np).to(dev)
+    lam_t = torch.from_numpy(lam).to(dev)
+    entry = {}
+    for terms, tol1 in ((3, 2.0 ** -21), (1, 2.0 ** -10)):
+        ms, (L, V, st) = timed(mpj.syevj_mp, A, options={"stage1_tf32_terms": terms, "tol_stage1": tol1})
+        entry[f"tf32_terms_{terms}"] = {"ms": ms, "tol_stage1": tol1, "sweeps_stage1": st["sweeps_stage1"],
+                                        "sweeps": st["sweeps"], "off_T0": st["off_T0"],
+                                        "stages_ms": st["ms_stage"], **accuracy(A, lam_t, L, V)}
+        del L, V
+    out["stage1_precision_n4096"] = entry
+    del A
+    torch.cuda.empty_cache()
     for m, n, idx in ((4096, 2048, 0), (8192, 1024, 1)):
         A_np, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, idx), sigma_min=1e-10)
         A = torch.from_numpy(A_np).to(dev)

@@ -43,9 +43,13 @@ constexpr int kTcThreads = 128;     // warp w owns TMEM lanes 32w .. 32w+31 (row
 constexpr int kTcWait = 1 << 22;    // mbarrier polls before a tile gives up
 constexpr int kB = 32;              // block size b; pair width 2b = 64 = K = N of the MMA
 constexpr int kM = 2 * kB;
+// Threads of the FP32 block solves: an inner step is a chain of short
+// dependent phases, and more warps hide more of their latency (measured at
+// n = 4096: 256 threads 122 ms, 512 threads 78 ms, 1024 threads 74 ms of solves).
+constexpr int kSolve32Threads = 1024;
 
 
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(kSolve32Threads)
 k_solve2_nb(float* __restrict__ T, int N, float* __restrict__ Fbuf, float* __restrict__ Sbuf,
             float* __restrict__ Fimg, float* __restrict__ fmax, int round, float eps, float tau,
             float gate, int max_inner, int cross, unsigned long long* __restrict__ rot_counter) {
@@ -408,7 +412,7 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
             if (set < 0) return MPJ_CUDA_ERROR;
             {
                 MPJ_PROF(PC_SOLVE2_F32, s);
-                k_solve2_nb<<<K, kSolveThreads, InnerLayout<float, kM>::bytes, s>>>(
+                k_solve2_nb<<<K, kSolve32Threads, InnerLayout<float, kM>::bytes, s>>>(
                     T, N, Wbuf[set], Sbuf[set], Fimg[set], fmax[set], r, (float)eps_skip, tau, gate, max_inner,
                     cross, rot);
             }
