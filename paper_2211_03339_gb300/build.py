@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmpjacobi.so")
-SOURCES = ["api.cu", "kernels.cu", "twosided.cu", "onesided.cu", "gemm64.cu", "mgs.cu", "prof.cu", "batched.cu", "backward.cu", "tc_apply.cu", "ozaki.cu", "tc64_apply.cu"]
+SOURCES = ["api.cu", "kernels.cu", "twosided.cu", "onesided.cu", "gemm64.cu", "mgs.cu", "prof.cu", "batched.cu", "backward.cu", "tc_apply.cu", "ozaki.cu", "tc64_apply.cu", "tc64_onesided.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-Xptxas", "-warn-spills"]

@@ -302,8 +302,9 @@ int svd_layout(Arena& a, int m, int n, int N, int B, bool mp, SvdBufs& b) {
     b.Q = mp ? a.take<double>(nn) : nullptr;
     b.C32 = mp ? a.take<float>(mN) : nullptr;
     b.V32 = mp ? a.take<float>(NN) : nullptr;
-    b.eng = a.take<char>(max2(onesided_workspace_bytes<double>(m, N, B),
-                              onesided_workspace_bytes<float>(m, N, B)));
+    b.eng = a.take<char>(max2(max2(onesided_workspace_bytes<double>(m, N, B),
+                                   onesided_workspace_bytes<float>(m, N, B)),
+                              onesided_tc64_supported(m, N, B) ? onesided_tc64_workspace_bytes(m, N) : 0));
     b.mgsw = mp ? a.take<char>(mgs_workspace_bytes(n, n)) : nullptr;
     b.ozA = mp ? a.take<char>(oz_operand_bytes(m, n)) : nullptr;
     b.ozQ = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
@@ -394,8 +395,13 @@ int gesvj_impl(bool mp, const double* A, int m, int n, int lda, double* Sigma, d
         MPJ_TRY(set_identity_f64(b.V64, N, N, N, s));
         tm.mark(1); tm.mark(2); tm.mark(3);
     }
-    MPJ_TRY(onesided_sweeps<double>(b.C64, m, b.V64, m, N, n, B, tol, op.ju_ratio, op.max_sweeps,
-                                    op.max_inner, b.eng, s, &r2));                         // steps 4-10
+    if (!knobs().simt_sweeps && onesided_tc64_supported(m, N, B)) {                        // steps 4-10
+        MPJ_TRY(onesided_sweeps_tc64(b.C64, b.V64, m, N, n, tol, op.ju_ratio, op.max_sweeps, op.max_inner, b.eng,
+                                     s, &r2));
+    } else {
+        MPJ_TRY(onesided_sweeps<double>(b.C64, m, b.V64, m, N, n, B, tol, op.ju_ratio, op.max_sweeps,
+                                        op.max_inner, b.eng, s, &r2));
+    }
     MPJ_TRY(colnorms_f64(b.C64, m, m, n, b.nrm, s));                                       // steps 11-13
     MPJ_TRY(rank_sort(b.nrm, 1, n, true, b.sc.perm, s));
     MPJ_TRY(svd_post(b.C64, m, b.V64, N, b.nrm, b.sc.perm, m, n, Sigma, U, ldu, V, ldv, b.sc.flag, s));

@@ -113,7 +113,8 @@ enum ProfClass {
     PC_SOLVE2_F32 = 0, PC_APPLY2_F32, PC_SOLVE2_F64, PC_APPLY2_F64, PC_DGEMM, PC_MGS_PANEL,
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
     PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2_F32,
-    PC_OZ_SLICE, PC_OZ_GEMM, PC_TCV_F32, PC_TCP1_F64, PC_TCP2_F64, PC_TCV_F64, kProfClasses
+    PC_OZ_SLICE, PC_OZ_GEMM, PC_TCV_F32, PC_TCP1_F64, PC_TCP2_F64, PC_TCV_F64, PC_GRAM_TC64,
+    PC_TCC_F64, PC_TCV1_F64, kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -163,6 +164,12 @@ size_t tc64_workspace_bytes(int N);
 bool tc64_supported(int N, int B);
 int twosided_sweeps_tc64(double* T, double* V, int N, int n, double tol_abs, double eps_skip, int max_sweeps,
                          int max_inner, int cross, void* work, cudaStream_t s, SweepResult* res);
+// One-sided FP64 sweeps with the block Grams and rotations on the tensor cores
+// (tc64_onesided.cu): b = 32, N a multiple of 64, m even and >= 128.
+bool onesided_tc64_supported(int m, int N, int B);
+size_t onesided_tc64_workspace_bytes(int m, int N);
+int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_rot, double ju_ratio,
+                         int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res);
 // Z[:, c] = V[:, perm[c]] (widened) from a row-major V.
 int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double* Z, int ldz,
                         cudaStream_t s);

@@ -29,7 +29,7 @@ const char* kNames[kProfClasses] = {
     "solve2_f32", "apply2_f32", "solve2_f64", "apply2_f64", "dgemm_f64", "mgs_panel",
     "mgs_proj", "gram1_f32", "solve1_f32", "apply1_f32", "gram1_f64", "solve1_f64",
     "apply1_f64", "aux", "apply2v_f32", "apply2v_f64", "batched", "tc1_f32", "tc2_f32", "oz_slice", "oz_gemm", "tcv_f32",
-    "tcp1_f64", "tcp2_f64", "tcv_f64"};
+    "tcp1_f64", "tcp2_f64", "tcv_f64", "gram_tc64", "tcc_f64", "tcv1_f64"};
 }  // namespace
 
 ProfScope::ProfScope(int cls_, cudaStream_t s_) : cls(cls_), s(s_) {

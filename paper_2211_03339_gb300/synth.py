@@ -127,6 +127,15 @@ def svd_matrix(m: int, n: int, seed: int = 0, sigma_min: float = 1e-10):
     return np.asfortranarray(A), sigma, U, V
 
 
+def graded_matrix(m: int, n: int, seed: int = 0, decades: float = 12.0):
+    """A = B D column-major: B m x n Gaussian (well conditioned for m well above n),
+    D diagonal with entries 10^(-decades * k / (n - 1)) in a random column order."""
+    rng = rng_for(seed)
+    B = rng.standard_normal((m, n))
+    d = 10.0 ** (-decades * np.arange(n) / max(n - 1, 1))
+    return np.asfortranarray(B * rng.permutation(d)[None, :])
+
+
 def batch_sizes(count: int, lo: int, hi: int, seed: int) -> np.ndarray:
     """Sizes n_i uniform in [lo, hi] for a batched workload."""
     return rng_for(seed).integers(lo, hi + 1, size=count)

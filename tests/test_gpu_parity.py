@@ -8,6 +8,7 @@ The oracle runs at sizes it finishes in seconds (several 64-wide tiles plus a
 ragged tail); the full-size cases are checked through properties that hold at
 any size (residual, orthogonality, the constructed spectrum).
 """
+import functools
 import os
 
 import numpy as np
@@ -253,6 +254,49 @@ def test_gesvj_parity(mpj, m, n, method):
     assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
     assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
     assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
+
+
+@functools.lru_cache(maxsize=1)
+def _oracle_sigma_520x448():
+    A = synth.svd_matrix(520, 448, seed=synth.seed_for(2, 7), sigma_min=1e-10)[0]
+    return oracle.gesvj_plain(A)[0]
+
+
+@pytest.mark.parametrize("method", ["mp", "plain"])
+def test_gesvj_tensor_core_sweeps_vs_simt(mpj, method):
+    """The FP64 one-sided sweeps with exactly split Grams and rotations on the tensor
+    cores (n > 256: b = 32, N = 448, m = 520 rows: four full slabs and a ragged one)
+    and the SIMT engine (MPJ_OPT_SIMT_SWEEPS) on the same matrix, both against the
+    oracle's singular values."""
+    m, n = 520, 448
+    A, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, 7), sigma_min=1e-10)
+    So = _oracle_sigma_520x448()
+    f = mpj.gesvj_mp if method == "mp" else mpj.gesvj_plain
+    for flags in (0, mpj.OPT_SIMT_SWEEPS):
+        Sg, Ug, Vg, st = f(dev(A), options={"flags": flags, "max_sweeps": 100})
+        Sg, Ug, Vg = host(Sg), host(Ug), host(Vg)
+        assert (np.diff(Sg) <= 0).all()
+        assert np.abs(Sg - So).max() <= 10 * n * U * sig[0]
+        assert np.linalg.norm(A @ Vg - Ug * Sg) / np.linalg.norm(A) <= 10 * n * U
+        assert np.linalg.norm(Vg.T @ Vg - np.eye(n)) <= 10 * n * U
+        assert np.linalg.norm(Ug.T @ Ug - np.eye(n)) <= 10 * n * U
+
+
+@pytest.mark.parametrize("flags", ["tensor", "simt"])
+def test_gesvj_plain_graded_relative_accuracy(mpj, flags):
+    """One-sided Jacobi keeps every singular value of a column-graded A = B D (B
+    Gaussian 600 x 320, D over 12 decades) to high relative accuracy.  On the
+    tensor cores the digits of C are scaled per column, so a small column is not
+    cut relative to a large one in the same rows; a per-row scale would leave the
+    small singular values with errors relative to the largest."""
+    m, n = 600, 320
+    A = synth.graded_matrix(m, n, seed=synth.seed_for(2, 11), decades=12.0)
+    So = oracle.gesvj_plain(A)[0]
+    opts = {"max_sweeps": 100, "flags": mpj.OPT_SIMT_SWEEPS if flags == "simt" else 0}
+    Sg, Ug, Vg, st = mpj.gesvj_plain(dev(A), options=opts)
+    Sg = host(Sg)
+    assert So.min() < 1e-11 * So.max()
+    assert (np.abs(Sg - So) / So).max() <= 1e-11
 
 
 def test_gesvj_full_size_properties(mpj):
