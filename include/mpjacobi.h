@@ -93,6 +93,9 @@ typedef struct mpj_options {
 #define MPJ_OPT_MGS_GLOBAL   16   /* MGS panels from global memory instead of the shared
                                      memory of a thread-block cluster                     */
 #define MPJ_OPT_TRACE        32   /* per-sweep rotation counts and off-norms on stderr    */
+#define MPJ_OPT_FP64_SOLVES  64   /* one-sided tensor-core sweeps: block solves keep the
+                                     Gram matrix in FP64 (default: FP32 off-diagonal,
+                                     FP64 diagonal and rotations, where the range allows)  */
 
 /* ------------------------------------------------------------------------
  * Symmetric eigendecomposition A = V diag(Lambda) V^T.

@@ -76,6 +76,7 @@ OPT_FP64_PRODUCTS = 4
 OPT_FULL_INNER = 8
 OPT_MGS_GLOBAL = 16
 OPT_TRACE = 32
+OPT_FP64_SOLVES = 64
 
 
 class BatchTuning(ctypes.Structure):

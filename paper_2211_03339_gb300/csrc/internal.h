@@ -97,6 +97,7 @@ struct Knobs {
     bool full_inner = false;    // tensor-core FP64 sweeps: full inner tournament
     bool mgs_global = false;    // MGS panels from global memory
     bool trace = false;         // per-sweep trace on stderr
+    bool fp64_solves = false;   // one-sided tensor-core solves: S kept in FP64
     int stage1_terms = 3;       // TF32 products per tile of the FP32 stage: 3 or 1
 };
 const Knobs& knobs();
@@ -165,7 +166,7 @@ bool tc64_supported(int N, int B);
 int twosided_sweeps_tc64(double* T, double* V, int N, int n, double tol_abs, double eps_skip, int max_sweeps,
                          int max_inner, int cross, void* work, cudaStream_t s, SweepResult* res);
 // One-sided FP64 sweeps with the block Grams and rotations on the tensor cores
-// (tc64_onesided.cu): b = 32, N a multiple of 64, m even and >= 128.
+// (tc64_onesided.cu): b = 32, N a multiple of 64, m even, 128 <= m < 2^20.
 bool onesided_tc64_supported(int m, int N, int B);
 size_t onesided_tc64_workspace_bytes(int m, int N);
 int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_rot, double ju_ratio,

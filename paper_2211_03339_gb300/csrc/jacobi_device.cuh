@@ -38,6 +38,44 @@ __device__ __forceinline__ void rotation_cs(Real app, Real aqq, Real apq, Real& 
 
 template <class Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
 
+// Lemma 3.1 in FP64 with reciprocals and reciprocal square roots in place of
+// the divisions and square roots (a few ulps in t, c, s; the serial chain of a
+// step's rotations is a fraction as long, and on this GPU the block solves wait
+// on that chain).  For |mu| > 2^26, t = 1/(2 mu) to working precision.  Also
+// returns c - 1 = -s^2 / (1 + c) without cancellation.
+__device__ __forceinline__ void rotation_cs_fast(double app, double aqq, double apq, double& c, double& s,
+                                                 double& cm, double& t) {
+    const double mu = (aqq - app) * (0.5 * __drcp_rn(apq));
+    const double am = mu < 0.0 ? -mu : mu;
+    if (am > 67108864.0) {
+        t = 0.5 * __drcp_rn(mu);
+    } else {
+        const double h = fma(mu, mu, 1.0);
+        t = __drcp_rn(am + h * rsqrt(h));
+        if (mu < 0.0) t = -t;
+    }
+    c = rsqrt(fma(t, t, 1.0));
+    s = t * c;
+    cm = -(s * s) * __drcp_rn(1.0 + c);
+}
+
+// The rotation of a mixed-precision one-sided solve (Lemma 5.1 on a Gram
+// matrix, FP64 diagonal, FP32 entry): t in FP32, whose error only perturbs the
+// angle, then c, s and c - 1 in FP64 from that t, so that the rotation is
+// orthogonal to working precision.
+__device__ __forceinline__ void rotation_cs_mixed(double app, double aqq, float apq, double& c, double& s,
+                                                  double& cm, double& t) {
+    const float mu = (float)(aqq - app) / (2.0f * apq);
+    const float am = fabsf(mu);
+    float tf;
+    if (am > 1.0e9f) tf = 0.5f / mu;
+    else tf = copysignf(1.0f / (am + sqrtf(fmaf(mu, mu, 1.0f))), mu);
+    t = (double)tf;
+    c = rsqrt(fma(t, t, 1.0));
+    s = t * c;
+    cm = -(s * s) * __drcp_rn(1.0 + c);
+}
+
 // Shared-memory footprint of a block-pair solve for M = 2b: S, F and a third
 // M x (M+1) buffer (the Gram/correction matrix of the re-orthogonalisation),
 // two buffers of c, s, c-1, t of the M/2 rotations of a step, two buffers of
@@ -79,14 +117,19 @@ __device__ __forceinline__ int step_rotations(const Real* S, Real* cs, int* ip, 
         }
         if (p > q) { int t = p; p = q; q = t; }
         Real apq = S[q * LD + p], app = S[p * LD + p], aqq = S[q * LD + q];
-        Real c = Real(1), s = Real(0), t = Real(0);
+        Real c = Real(1), s = Real(0), t = Real(0), cm = Real(0);
         int skip = 1;
         Real aa = rabs(apq);
         if (apq != Real(0) && aa > tau && !(aa <= eps * sqrt(rabs(app * aqq)))) {
-            rotation_cs(app, aqq, apq, c, s, t);
+            if constexpr (sizeof(Real) == 8) {
+                rotation_cs_fast(app, aqq, apq, c, s, cm, t);
+            } else {
+                rotation_cs(app, aqq, apq, c, s, t);
+                cm = -(s * s) / (Real(1) + c);
+            }
             skip = 0;
         }
-        cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = -(s * s) / (Real(1) + c); cs[3 * P + tid] = t;
+        cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = cm; cs[3 * P + tid] = t;
         ip[tid] = p; ip[P + tid] = q; ip[2 * P + tid] = skip;
         mine = !skip;
     }
@@ -215,6 +258,31 @@ __device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int
     }
 }
 
+// step_update_f restricted to rows [row0, row0 + nrows) of F (items (row, rotation)),
+// for solves whose F rows are spread over the CTAs of a cluster.
+template <class Real, int M>
+__device__ __forceinline__ void step_update_f_rows(Real* F, const Real* cs, const int* ip, int t0, int nt, int row0,
+                                                   int nrows) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    const Real* sn = cs + P;
+    const Real* cm = cs + 2 * P;
+    const int* iq = ip + P;
+    const int* sk = ip + 2 * P;
+    for (int t = t0; t < nrows * P; t += nt) {
+        const int a = t / nrows, row = row0 + (t - a * nrows);
+        if (sk[a]) continue;
+        const int pa = ip[a], qa = iq[a];
+        const Real c = cs[a], s = sn[a];
+        const Real fp = F[pa * LD + row], fq = F[qa * LD + row];
+        Real np = c * fp - s * fq, nq = s * fp + c * fq;
+        if (row == pa) { np += cm[a]; nq += s; }
+        else if (row == qa) { np -= s; nq += cm[a]; }
+        F[pa * LD + row] = np;
+        F[qa * LD + row] = nq;
+    }
+}
+
 // Cyclic Jacobi on the symmetric M x M matrix S (shared, column-major, ld M+1).
 // The accumulated rotation W = J_1 J_2 ... is kept as F = W - I (F must hold
 // the start, e.g. 0): F <- F J + (J - I), so that the rounding errors of F are
@@ -224,7 +292,8 @@ __device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int
 // skipped (its entry set to zero, not counted) when |s_pq| <= eps sqrt(|s_pp s_qq|)
 // (Remark 3.7) or |s_pq| <= tau (entries that cannot matter for the stopping
 // test).  Stops after an inner sweep with no rotation or after max_inner
-// sweeps.  Returns the number of rotations applied (all threads).
+// sweeps.  Returns the number of rotations applied (all threads).  With
+// nrows < M only rows [row0, row0 + nrows) of F are accumulated.
 // Must be called by all threads of the block (any multiple of 32, at least 256,
 // so that three S-update items per thread cover the P(P+1)/2 <= 528 blocks).
 // With cross_round >= 0 an inner sweep is the M/2 steps that rotate every pair
@@ -238,7 +307,7 @@ __device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int
 // step r into F; the step arrays are double buffered.
 template <class Real, int M>
 __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real tau, int max_inner,
-                            int cross_round = -1) {
+                            int cross_round = -1, int row0 = 0, int nrows = M) {
     constexpr int P = M / 2;
     static_assert(P <= 32, "pair count must fit one warp");
     volatile int* cnt = ip + 6 * P;  // [0] applied in this sweep
@@ -262,6 +331,9 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
             if (more && tid < 32)
                 applied += step_rotations<Real, M>(S, cs + (cur ^ 1) * 4 * P, ip + (cur ^ 1) * 3 * P, r + 1,
                                                    cross_round, eps, tau);
+            else if (nrows != M)
+                step_update_f_rows<Real, M>(F, csc, ipc, more ? tid - 32 : tid, more ? blockDim.x - 32 : blockDim.x,
+                                            row0, nrows);
             else if (more)
                 step_update_f<Real, M>(F, csc, ipc, tid - 32, blockDim.x - 32);
             else
@@ -271,6 +343,145 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
         if (tid == 0) cnt[0] = applied;
         __syncthreads();
         int c = cnt[0];
+        __syncthreads();
+        total += c;
+        if (c == 0) break;
+    }
+    return total;
+}
+
+// ---------------------------------------------------------------- mixed precision
+// inner_jacobi for a problem whose S only steers the rotations (the Gram matrix
+// of a one-sided solve: C and V change through W alone).  S is held as an FP64
+// diagonal dg and an FP32 off-diagonal E (both scaled by the same power of two,
+// ld M+1, diagonal entries of E unused); the Rutishauser update moves the
+// diagonal in FP64 (d_p - t e_pq, d_q + t e_pq) and E is rotated in FP32, so
+// the rounding of E is relative to the off-diagonal entries themselves.  The
+// rotations (Lemma 5.1 on the Gram matrix, Lemma 3.1 form) are formed in FP64
+// from dg and E (the tangent in FP32, rotation_cs_mixed) and F = W - I is
+// accumulated in FP64 as in inner_jacobi, so W stays orthogonal to working
+// precision; FP32 rounding in E and t only perturbs the angles (a convergence
+// effect).  csf holds FP32 copies of (c, s) of the two
+// step buffers (4 (M/2) floats).
+template <int M>
+__device__ __forceinline__ int step_rotations_mixed(const double* dg, const float* E, double* cs, float* csf, int* ip,
+                                                    int r, int cross_round, double eps) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    const int tid = threadIdx.x;
+    int mine = 0;
+    if (tid < P) {
+        int p, q;
+        if (cross_round < 0) {
+            p = rr_index(r, tid, M);
+            q = rr_index(r, M - 1 - tid, M);
+        } else if (r < P) {
+            p = tid;
+            q = P + (tid + r) % P;
+        } else {
+            const int qr = cross_round % (P - 1), h = tid / (P / 2), i = tid % (P / 2);
+            p = h * P + rr_index(qr, i, P);
+            q = h * P + rr_index(qr, P - 1 - i, P);
+        }
+        if (p > q) { int t = p; p = q; q = t; }
+        const float ef = E[q * LD + p];
+        const double apq = (double)ef, app = dg[p], aqq = dg[q];
+        double c = 1.0, s = 0.0, t = 0.0, cm = 0.0;
+        int skip = 1;
+        // |s_pq| > eps sqrt(|s_pp s_qq|) as squares (the scaled entries are at most 2)
+        if (ef != 0.f && apq * apq > (eps * eps) * rabs(app * aqq)) {
+            rotation_cs_mixed(app, aqq, ef, c, s, cm, t);
+            skip = 0;
+        }
+        cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = cm; cs[3 * P + tid] = t;
+        csf[tid] = (float)c; csf[P + tid] = (float)s;
+        ip[tid] = p; ip[P + tid] = q; ip[2 * P + tid] = skip;
+        mine = !skip;
+    }
+    return __popc(__ballot_sync(0xffffffffu, mine));
+}
+
+template <int M>
+__device__ __forceinline__ void step_update_s_mixed(double* dg, float* E, const double* cs, const float* csf,
+                                                    const int* ip, const int (&items)[3]) {
+    constexpr int LD = M + 1;
+    constexpr int P = M / 2;
+    const double* tt = cs + 3 * P;
+    const float* snf = csf + P;
+    const int* iq = ip + P;
+    const int* sk = ip + 2 * P;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (items[k] < 0) continue;
+        const int a = items[k] & 255, b = items[k] >> 8;
+        const int pa = ip[a], qa = iq[a];
+        if (a == b) {
+            // a skipped pair (t = 0) keeps its diagonal and loses its entry, as in inner_jacobi
+            const double apq = (double)E[qa * LD + pa], ta = tt[a];
+            dg[pa] = dg[pa] - ta * apq;
+            dg[qa] = dg[qa] + ta * apq;
+            E[qa * LD + pa] = 0.f;
+            E[pa * LD + qa] = 0.f;
+        } else {
+            if (sk[a] && sk[b]) continue;
+            const int pb = ip[b], qb = iq[b];
+            const float ca = csf[a], sa = snf[a], cb = csf[b], sb = snf[b];
+            const float x00 = E[pb * LD + pa], x01 = E[qb * LD + pa];
+            const float x10 = E[pb * LD + qa], x11 = E[qb * LD + qa];
+            const float y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
+            const float y10 = sa * x00 + ca * x10, y11 = sa * x01 + ca * x11;
+            const float z00 = cb * y00 - sb * y01, z01 = sb * y00 + cb * y01;
+            const float z10 = cb * y10 - sb * y11, z11 = sb * y10 + cb * y11;
+            E[pb * LD + pa] = z00; E[qb * LD + pa] = z01;
+            E[pb * LD + qa] = z10; E[qb * LD + qa] = z11;
+            E[pa * LD + pb] = z00; E[pa * LD + qb] = z01;
+            E[qa * LD + pb] = z10; E[qa * LD + qb] = z11;
+        }
+    }
+}
+
+// Same schedule, counting and stopping rule as inner_jacobi (tau = 0).  With
+// nrows < M only rows [row0, row0 + nrows) of F are accumulated (the other CTAs
+// of a cluster, which form the same rotations, hold the rest).
+template <int M>
+__device__ int inner_jacobi_mixed(double* dg, float* E, double* F, double* cs, float* csf, int* ip, double eps,
+                                  int max_inner, int cross_round = -1, int row0 = 0, int nrows = M) {
+    constexpr int P = M / 2;
+    static_assert(P <= 32, "pair count must fit one warp");
+    volatile int* cnt = ip + 6 * P;
+    const int tid = threadIdx.x;
+    const int nsteps = cross_round >= 0 ? P + 1 : M - 1;
+    int items[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) items[k] = upper_item<P>(tid + k * (int)blockDim.x);
+    int total = 0;
+    for (int sweep = 0; sweep < max_inner; ++sweep) {
+        int applied = 0;
+        if (tid < 32) applied += step_rotations_mixed<M>(dg, E, cs, csf, ip, 0, cross_round, eps);
+        __syncthreads();
+        for (int r = 0; r < nsteps; ++r) {
+            const int cur = r & 1;
+            const double* csc = cs + cur * 4 * P;
+            const float* csfc = csf + cur * 2 * P;
+            const int* ipc = ip + cur * 3 * P;
+            step_update_s_mixed<M>(dg, E, csc, csfc, ipc, items);
+            __syncthreads();
+            const bool more = r + 1 < nsteps;
+            if (more && tid < 32)
+                applied += step_rotations_mixed<M>(dg, E, cs + (cur ^ 1) * 4 * P, csf + (cur ^ 1) * 2 * P,
+                                                   ip + (cur ^ 1) * 3 * P, r + 1, cross_round, eps);
+            else if (nrows != M)
+                step_update_f_rows<double, M>(F, csc, ipc, more ? tid - 32 : tid,
+                                              more ? blockDim.x - 32 : blockDim.x, row0, nrows);
+            else if (more)
+                step_update_f<double, M>(F, csc, ipc, tid - 32, blockDim.x - 32);
+            else
+                step_update_f<double, M>(F, csc, ipc, tid, blockDim.x);
+            __syncthreads();
+        }
+        if (tid == 0) cnt[0] = applied;
+        __syncthreads();
+        const int c = cnt[0];
         __syncthreads();
         total += c;
         if (c == 0) break;

@@ -130,6 +130,7 @@ KnobScope::KnobScope(const mpj_options* o) : saved(g_knobs) {
         k.full_inner = (o->flags & MPJ_OPT_FULL_INNER) != 0;
         k.mgs_global = (o->flags & MPJ_OPT_MGS_GLOBAL) != 0;
         k.trace = (o->flags & MPJ_OPT_TRACE) != 0;
+        k.fp64_solves = (o->flags & MPJ_OPT_FP64_SOLVES) != 0;
         if (o->stage1_tf32_terms == 1 || o->stage1_tf32_terms == 3) k.stage1_terms = o->stage1_tf32_terms;
     }
     g_knobs = k;

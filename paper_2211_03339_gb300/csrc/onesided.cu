@@ -123,7 +123,7 @@ template <class Real, int B>
 __global__ void __launch_bounds__(kSolveThreads)
 k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
          Real* __restrict__ Fbuf, Real tol_rot,
-         Real gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
+         Real gate, int max_inner, int cross_round, unsigned long long* __restrict__ rot_counter) {
     constexpr int M = 2 * B;
     constexpr int LD = M + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -149,7 +149,7 @@ k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
         F[c * LD + r] = Real(0);
     }
     __syncthreads();
-    int applied = inner_jacobi<Real, M>(S, F, cs, ip, tol_rot, Real(0), max_inner);
+    int applied = inner_jacobi<Real, M>(S, F, cs, ip, tol_rot, Real(0), max_inner, cross_round);
     finish_block<Real, M>(F, G2, Fbuf + (size_t)blockIdx.x * M * M, gate, flag, nullptr);
     if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
 }
@@ -217,7 +217,7 @@ static int configure_onesided() {
 template <class Real, int B>
 static int launch_round1(Real* C, int ldc, Real* V, int m, int N, Real* Wbuf, Real* Ghi, Real* Glo,
                          int nsplit, int rows_per, int r, Real tol_rot, Real gate, int max_inner,
-                         int comp, unsigned long long* rot, cudaStream_t s) {
+                         int comp, int cross, unsigned long long* rot, cudaStream_t s) {
     constexpr int M = 2 * B;
     const int K = N / M;
     dim3 g(K, nsplit);
@@ -226,7 +226,7 @@ static int launch_round1(Real* C, int ldc, Real* V, int m, int N, Real* Wbuf, Re
     MPJ_LAUNCH_CHECK("k_gram1");
     { MPJ_PROF(sizeof(Real) == 8 ? PC_SOLVE1_F64 : PC_SOLVE1_F32, s);
     k_solve1<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(Ghi, Glo, nsplit, Wbuf, tol_rot,
-                                                                      gate, max_inner, rot); }
+                                                                      gate, max_inner, cross ? r : -1, rot); }
     MPJ_LAUNCH_CHECK("k_solve1");
     int n_ctiles = ((m + M - 1) / M) * K;
     int n_vtiles = (N / M) * K;
@@ -278,15 +278,18 @@ int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, doubl
     const bool dbl = sizeof(Real) == 8;
     const double comp_switch = dbl ? kCompSwitch : -1.0;
     int comp = 0;
+    // FP32: the cross-pair inner schedule of inner_jacobi once the rounds of a
+    // sweep cover the intra-block tournament (N >= b^2); FP64 keeps the full one
+    const int cross = !dbl && N >= B * B && !knobs().full_inner;
     while (res->sweeps < max_sweeps) {
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
         for (int r = 0; r < rounds; ++r) {
             if (B == 16) {
                 MPJ_TRY((launch_round1<Real, 16>(C, ldc, V, m, N, Wbuf, Ghi, Glo, nsplit, rows_per, r,
-                                                 (Real)tol_rot, gate, max_inner, comp, rot, s)));
+                                                 (Real)tol_rot, gate, max_inner, comp, cross, rot, s)));
             } else {
                 MPJ_TRY((launch_round1<Real, 32>(C, ldc, V, m, N, Wbuf, Ghi, Glo, nsplit, rows_per, r,
-                                                 (Real)tol_rot, gate, max_inner, comp, rot, s)));
+                                                 (Real)tol_rot, gate, max_inner, comp, cross, rot, s)));
             }
         }
         MPJ_CUDA_TRY(cudaMemcpyAsync(hs.u, rot, sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));

@@ -25,8 +25,9 @@
 // 256 rows between two drains |T_d| < 10 2^20 < 2^24 (exact in the FP32 TMEM
 // accumulators and in their conversion to int32), and over at most 8192 rows
 // per CTA the int32 totals stay below 2^29 and hi, lo below 2^50 (exact in
-// FP64).  G_ij leaves the kernel as the exact pair hi 2^28 + lo (TwoSum), the
-// form the solve sums compensated over the row ranges.  The dropped levels
+// FP64).  A CTA writes the integers hi and lo of its row range; the solve adds
+// them over the row ranges exactly (64-bit integers) and rounds
+// 2^(E_i + E_j - 2107) (hi 2^28 + lo) to FP64 once.  The dropped levels
 // d >= 8 and the truncated digits put an error of at most about
 // 2^-54 (||c_i||_1 max|c_j| + ||c_j||_1 max|c_i|) on g_ij, independent of the
 // other columns' scales: the cosines that decide the rotations are accurate to
@@ -34,8 +35,12 @@
 #include <cmath>
 #include <cstdio>
 
+#include <cooperative_groups.h>
+
 #include "internal.h"
 #include "tc64_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace mpj {
 
@@ -52,6 +57,7 @@ constexpr int kGThr = 448;                   // warp 0 TMA, 1 MMA, 2-9 slicers, 
 constexpr int kGDrainThr = 128;
 constexpr int kGramCtas = 152;               // target CTA count of a Gram launch (one per SM)
 constexpr size_t kGramSmem = 2 * (size_t)kGXBytes + 2 * (size_t)kGSlot + 1024;
+constexpr int kNoMixed = 1 << 20;            // k_solve1_tc64: S stays FP64
 
 __device__ __forceinline__ void tmem_ld16u(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
@@ -95,11 +101,12 @@ __device__ __forceinline__ double times_pow2(double x, int e) {
 //   warps 10-13 drain: every 4 chunks the FP32 levels (TMEM lanes 0-15 of each
 //              lane quarter: the M = 64 accumulator) are converted to int32 and
 //              added to totals kept in the lanes 16-31 that the M = 64 MMAs do
-//              not use; at the end the totals become hi 2^28 + lo.
+//              not use; at the end the totals become the integers hi and lo
+//              of G_ij = 2^(E_i + E_j - 2107) (hi 2^28 + lo) for this row range.
 // Every wait is bounded; a timeout sets *err and the roles leave their loops.
 __global__ void __launch_bounds__(kGThr, 1)
 k_gram_tc64(const __grid_constant__ CUtensorMap map, int m, int N, int round, int rows_per,
-            const int* __restrict__ ncls, double* __restrict__ Ghi, double* __restrict__ Glo,
+            const int* __restrict__ ncls, long long* __restrict__ Ghi, long long* __restrict__ Glo,
             unsigned long long* __restrict__ err) {
     extern __shared__ unsigned char smraw[];
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
@@ -269,12 +276,8 @@ k_gram_tc64(const __grid_constant__ CUtensorMap map, int m, int N, int round, in
                             hi = hi * 128 + (long long)(int)T[d][jj];
                             lo = lo * 128 + (long long)(int)T[d + 4][jj];
                         }
-                        const double a = __ll2double_rn(hi) * 268435456.0, bb = __ll2double_rn(lo);
-                        const double s = a + bb, z = s - a;
-                        const double e = (a - (s - z)) + (bb - z);
-                        const int ex = cls_s[i] + cls_s[j] - 2107;
-                        Ghi[gbase + (size_t)j * kM + i] = times_pow2(s, ex);
-                        Glo[gbase + (size_t)j * kM + i] = times_pow2(e, ex);
+                        Ghi[gbase + (size_t)j * kM + i] = hi;
+                        Glo[gbase + (size_t)j * kM + i] = lo;
                     }
                 }
             }
@@ -318,18 +321,26 @@ __device__ __forceinline__ void slice_record(const double (&x)[8], int c, int j,
                        digit_pair(v[6], v[7], p));
 }
 
-// The 2b x 2b solve of pair b: the Gram partials summed compensated (hi + lo
-// pairs), cyclic Jacobi (Lemma 5.1 rotations, relative threshold tol_rot),
+// The 2b x 2b solve of pair b: the integer Gram totals of the row ranges summed
+// exactly and rounded to FP64 once, cyclic Jacobi (Lemma 5.1 rotations, relative threshold tol_rot; with
+// cross_round >= 0 the cross-pair inner schedule of inner_jacobi; with mixed,
+// the FP32 off-diagonal of inner_jacobi_mixed where the diagonal range allows),
 // W = I + F (re-orthogonalised when some |F| >= gate), then the two digit
 // records: Fv = digits of F for the V pass (row scaling) and Fc = digits of
 // G = diag(2^(E_k - E*)) F with E* folded into its column classes, plus the E_k,
 // for the C pass (column scaling).  Columns of an identity W keep their class
-// for the next round; the others get theirs from the C pass.
-__global__ void __launch_bounds__(kSolveThreads)
-k_solve1_tc64(const double* __restrict__ Ghi, const double* __restrict__ Glo, int nsplit, int N, int round,
+// for the next round; the others get theirs from the C pass.  Launched as
+// clusters of R CTAs per pair: each CTA repeats the cheap part (Gram sum, S
+// updates, rotations; bit-identical in every CTA) and accumulates M/R rows of F
+// in FP64, the part that bounds the solve; the leader gathers F through
+// distributed shared memory and finishes alone.
+__global__ void __launch_bounds__(kSolveThreads, 1)
+k_solve1_tc64(const long long* __restrict__ Ghi, const long long* __restrict__ Glo, int nsplit, int N, int round,
               double* __restrict__ Fbuf, float* __restrict__ fmax, unsigned char* __restrict__ Fv,
               unsigned char* __restrict__ Fc, const int* __restrict__ ncls_cur, int* __restrict__ ncls_nxt,
-              double tol_rot, double gate, int max_inner, unsigned long long* __restrict__ rot_counter) {
+              double tol_rot, double gate, int max_inner, int cross_round, int mixed,
+              unsigned long long* __restrict__ rot_counter) {
+    static_assert(kM * kM % kSolveThreads == 0, "entries per thread");
     constexpr int LD = kM + 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     double* S = reinterpret_cast<double*>(smraw);
@@ -339,27 +350,97 @@ k_solve1_tc64(const double* __restrict__ Ghi, const double* __restrict__ Glo, in
     int* ip = reinterpret_cast<int*>(cs + InnerLayout<double, kM>::kRealRot);
     int* flag = ip + InnerLayout<double, kM>::kFlagOffset;
     __shared__ int xc[kM];
-    __shared__ int ecmax_s;
-    const int b = blockIdx.x, t = threadIdx.x;
+    __shared__ int ecmax_s, mixed_s;
+    // R CTAs per pair (a cluster) form the same rotations; CTA `rank` accumulates
+    // rows [rank M/R, (rank+1) M/R) of F, which are gathered in the leader
+    cg::cluster_group cl = cg::this_cluster();
+    const int R = (int)cl.num_blocks(), rank = (int)cl.block_rank();
+    const int nrows = kM / R, row0 = rank * nrows;
+    const int b = blockIdx.x / R, t = threadIdx.x;
     int I, J;
     round_pair(round, b, N / kB, I, J);
     if (t < kM) xc[t] = ncls_cur[pair_global(t, I, J, kB)];
     const size_t off = (size_t)b * nsplit * kM * kM;
-    for (int q = t; q < kM * kM; q += blockDim.x) {
-        const int r = q % kM, c = q / kM;
-        double sacc = 0.0, cacc = 0.0;
+    __syncthreads();                                     // xc
+    {
+        // the row ranges' totals, exact: below 2^57 for m < 2^20 (16 loads in flight per thread)
+        constexpr int kPer = kM * kM / kSolveThreads;
+        long long hi[kPer], lo[kPer];
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) { hi[i] = 0; lo[i] = 0; }
         for (int sp = 0; sp < nsplit; ++sp) {
-            const size_t idx = off + (size_t)sp * kM * kM + (size_t)c * kM + r;
-            const double p = Ghi[idx];
-            const double tt = __dadd_rn(sacc, p), z = __dsub_rn(tt, sacc);
-            cacc = __dadd_rn(cacc, __dadd_rn(__dadd_rn(__dsub_rn(sacc, __dsub_rn(tt, z)), __dsub_rn(p, z)), Glo[idx]));
-            sacc = tt;
+            const size_t base = off + (size_t)sp * kM * kM;
+#pragma unroll
+            for (int i = 0; i < kPer; ++i) {
+                hi[i] += __ldg(Ghi + base + t + kSolveThreads * i);
+                lo[i] += __ldg(Glo + base + t + kSolveThreads * i);
+            }
         }
-        S[c * LD + r] = sacc + cacc;
-        F[c * LD + r] = 0.0;
+#pragma unroll
+        for (int i = 0; i < kPer; ++i) {
+            const int q = t + kSolveThreads * i, r = q % kM, c = q / kM;
+            const double v = fma(__ll2double_rn(hi[i]), 268435456.0, __ll2double_rn(lo[i]));
+            S[c * LD + r] = times_pow2(v, xc[r] + xc[c] - 2107);
+            F[c * LD + r] = 0.0;
+        }
     }
     __syncthreads();
-    const int applied = inner_jacobi<double, kM>(S, F, cs, ip, tol_rot, 0.0, max_inner);
+    // Mixed-precision solve (FP32 off-diagonal, inner_jacobi_mixed) when the
+    // diagonal spans at most 2^76: scaled by 2^-e (2^e <= d_max < 2^(e+1)), every
+    // entry above the threshold, |s_pq| > 2^-50 sqrt(s_pp s_qq) >= 2^-50 d_min,
+    // is then a normal FP32 number.
+    if (t < 32) {
+        const double a0 = S[t * LD + t], a1 = S[(t + 32) * LD + t + 32];
+        double mx = a0 > a1 ? a0 : a1;
+        double mn = a0 > 0.0 ? a0 : INFINITY;
+        if (a1 > 0.0 && a1 < mn) mn = a1;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ox = __shfl_xor_sync(0xffffffffu, mx, o), on = __shfl_xor_sync(0xffffffffu, mn, o);
+            mx = ox > mx ? ox : mx;
+            mn = on < mn ? on : mn;
+        }
+        if (t == 0) {
+            const int e = mx > 0.0 ? ilogb(mx) : 0;
+            mixed_s = mixed && mx > 0.0 && mn >= 0x1p-76 * mx && e >= -1000 && e <= 1000 ? e : kNoMixed;
+        }
+    }
+    __syncthreads();
+    int applied;
+    if (mixed_s != kNoMixed) {
+        const double sc = __longlong_as_double((long long)(1023 - mixed_s) << 52);
+        double v[kM * kM / kSolveThreads];
+#pragma unroll
+        for (int i = 0; i < kM * kM / kSolveThreads; ++i) {
+            const int q = t + kSolveThreads * i;
+            v[i] = S[(q / kM) * LD + q % kM] * sc;
+        }
+        __syncthreads();
+        float* E = reinterpret_cast<float*>(S);                       // M x (M+1) floats
+        double* dg = reinterpret_cast<double*>(E + kM * LD);          // then M doubles
+        float* csf = reinterpret_cast<float*>(dg + kM);               // then 4 (M/2) floats
+#pragma unroll
+        for (int i = 0; i < kM * kM / kSolveThreads; ++i) {
+            const int q = t + kSolveThreads * i, r = q % kM, c = q / kM;
+            E[c * LD + r] = (float)v[i];
+            if (r == c) dg[r] = v[i];
+        }
+        __syncthreads();
+        applied = inner_jacobi_mixed<kM>(dg, E, F, cs, csf, ip, tol_rot, max_inner, cross_round, row0, nrows);
+    } else {
+        applied = inner_jacobi<double, kM>(S, F, cs, ip, tol_rot, 0.0, max_inner, cross_round, row0, nrows);
+    }
+    if (R > 1) {
+        cl.sync();                                       // every CTA past its zeroing of F
+        if (rank != 0) {
+            double* F0 = cl.map_shared_rank(F, 0);
+            for (int q = t; q < kM * nrows; q += blockDim.x) {
+                const int c = q / nrows, k = row0 + q % nrows;
+                F0[c * LD + k] = F[c * LD + k];
+            }
+        }
+        cl.sync();                                       // the leader holds all of F
+        if (rank != 0) return;
+    }
     finish_block<double, kM>(F, G2, Fbuf + (size_t)b * kM * kM, gate, flag, fmax + b);
     __syncthreads();
     const bool ident = __uint_as_float(reinterpret_cast<const unsigned*>(flag)[1]) == 0.f;
@@ -401,7 +482,7 @@ void gram_split_tc(int m, int K, int* nsplit, int* rows_per) {
 }  // namespace
 
 bool onesided_tc64_supported(int m, int N, int B) {
-    return B == kB && N % kM == 0 && N >= kM && m >= kSlab && m % 2 == 0;
+    return B == kB && N % kM == 0 && N >= kM && m >= kSlab && m % 2 == 0 && m < (1 << 20);
 }
 
 size_t onesided_tc64_workspace_bytes(int m, int N) {
@@ -415,8 +496,8 @@ size_t onesided_tc64_workspace_bytes(int m, int N) {
         a.take<unsigned char>(K * kFplBytes);       // V pass records
         a.take<unsigned char>(K * kFplColBytes);    // C pass records
     }
-    a.take<double>(K * nsplit * kM * kM);           // Gram partials: hi
-    a.take<double>(K * nsplit * kM * kM);           //                lo
+    a.take<long long>(K * nsplit * kM * kM);        // Gram totals per row range: hi
+    a.take<long long>(K * nsplit * kM * kM);        //                            lo
     a.take<int>(2 * (size_t)N);                     // column classes, two rounds
     a.take<unsigned long long>(4);
     return a.used + 256;
@@ -425,7 +506,7 @@ size_t onesided_tc64_workspace_bytes(int m, int N) {
 int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_rot, double ju_ratio,
                          int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res) {
     if (!onesided_tc64_supported(m, N, kB)) {
-        set_error_msg("tensor-core one-sided engine: needs b = 32, N a multiple of 64, m even and >= 128");
+        set_error_msg("tensor-core one-sided engine: needs b = 32, N a multiple of 64, m even, 128 <= m < 2^20");
         return MPJ_BAD_ARG;
     }
     const int K = N / kM;
@@ -443,8 +524,8 @@ int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_r
         Fv[set] = ar.take<unsigned char>((size_t)K * kFplBytes);
         Fc[set] = ar.take<unsigned char>((size_t)K * kFplColBytes);
     }
-    double* Ghi = ar.take<double>((size_t)K * nsplit * kM * kM);
-    double* Glo = ar.take<double>((size_t)K * nsplit * kM * kM);
+    long long* Ghi = ar.take<long long>((size_t)K * nsplit * kM * kM);
+    long long* Glo = ar.take<long long>((size_t)K * nsplit * kM * kM);
     int* ncls = ar.take<int>(2 * (size_t)N);
     unsigned long long* rot = ar.take<unsigned long long>(4);     // [0] rotations, [1] error flag
     if (!Fc[1] || !Ghi || !Glo || !ncls || !rot) {
@@ -484,8 +565,19 @@ int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_r
     const int slabsV = (N + kSlab - 1) / kSlab, itemsV = slabsV * K;
     const int perV = 8;
     const int gridV = (itemsV + perV - 1) / perV;
-    const double gate = 1.0 / 67108864.0;                // 2^-26, as the SIMT FP64 one-sided engine
+    // Newton-Schulz re-orthogonalisation of W = I + F only when some |F| >= 2^-6:
+    // F is accumulated with rounding relative to |F|, so below that W is
+    // orthogonal to a few ulps (each NS step costs two 64^3 FP64 products, more
+    // than the whole inner sweep)
+    const double gate = 1.0 / 64.0;
     const double Npairs = 0.5 * (double)n * (double)(n - 1);
+    // cross-pair inner schedule once the rounds of a sweep cover the intra-block tournament
+    const bool cross = N >= kB * kB && !knobs().full_inner;
+    const int mixed = knobs().fp64_solves ? 0 : 1;
+    // CTAs per pair of a solve (cluster size): the largest of 8, 4, 2, 1 that keeps
+    // the launch within one CTA per SM
+    int R = 8;
+    while (R > 1 && K * R > nsm) R >>= 1;
     long long g = 0;                                     // rounds so far: parity of the class buffers
     while (res->sweeps < max_sweeps) {
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
@@ -501,9 +593,22 @@ int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_r
             MPJ_LAUNCH_CHECK("k_gram_tc64");
             {
                 MPJ_PROF(PC_SOLVE1_F64, s);
-                k_solve1_tc64<<<K, kSolveThreads, InnerLayout<double, kM>::bytes, s>>>(
-                    Ghi, Glo, nsplit, N, r, Fbuf[set], fmax[set], Fv[set], Fc[set], nc, nn, tol_rot, gate,
-                    max_inner, rot);
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)R;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)(K * R));
+                cfg.blockDim = dim3(kSolveThreads);
+                cfg.dynamicSmemBytes = InnerLayout<double, kM>::bytes;
+                cfg.stream = s;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                MPJ_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_solve1_tc64, (const long long*)Ghi, (const long long*)Glo,
+                                                nsplit, N, r, Fbuf[set], fmax[set], Fv[set], Fc[set],
+                                                (const int*)nc, nn, tol_rot, gate, max_inner, cross ? r : -1, mixed,
+                                                rot));
             }
             MPJ_LAUNCH_CHECK("k_solve1_tc64");
             MPJ_TRY(side.after_solve());
