@@ -60,20 +60,34 @@ __device__ __forceinline__ void rotation_cs_fast(double app, double aqq, double 
 }
 
 // The rotation of a mixed-precision one-sided solve (Lemma 5.1 on a Gram
-// matrix, FP64 diagonal, FP32 entry): t in FP32, whose error only perturbs the
-// angle, then c, s and c - 1 in FP64 from that t, so that the rotation is
-// orthogonal to working precision.
-__device__ __forceinline__ void rotation_cs_mixed(double app, double aqq, float apq, double& c, double& s,
-                                                  double& cm, double& t) {
+// matrix, FP64 diagonal, FP32 entry), in two parts.
+//   rotation_angle_mixed  FP32 (its error only perturbs the rotation's effect,
+//                         a convergence matter): t = tan(theta) from
+//                         mu = (a_qq - a_pp) / (2 a_pq), the difference taken in
+//                         FP64, and the half-angle tangent
+//                         tau = t / (1 + sqrt(1 + t^2)), |tau| <= tan(pi/8);
+//   rotation_from_tau     FP64, with r = 1 / (1 + tau^2) (an FP32 seed and two
+//                         Newton steps): c = (1 - tau^2) r, s = 2 tau r,
+//                         c - 1 = -2 tau^2 r, a rotation orthogonal to working
+//                         precision whose c - 1 has no cancellation.
+__device__ __forceinline__ void rotation_angle_mixed(double app, double aqq, float apq, float& tf, float& tauf) {
     const float mu = (float)(aqq - app) / (2.0f * apq);
     const float am = fabsf(mu);
-    float tf;
     if (am > 1.0e9f) tf = 0.5f / mu;
     else tf = copysignf(1.0f / (am + sqrtf(fmaf(mu, mu, 1.0f))), mu);
-    t = (double)tf;
-    c = rsqrt(fma(t, t, 1.0));
-    s = t * c;
-    cm = -(s * s) * __drcp_rn(1.0 + c);
+    tauf = tf / (1.0f + sqrtf(fmaf(tf, tf, 1.0f)));
+}
+__device__ __forceinline__ void rotation_from_tau(float tauf, double& c, double& s, double& cm) {
+    const float seed = 1.0f / fmaf(tauf, tauf, 1.0f);
+    const double tau = (double)tauf;
+    const double t2 = tau * tau;                     // exact: tau has 24 bits
+    const double x = 1.0 + t2;
+    double r = (double)seed;
+    r = fma(r, fma(-x, r, 1.0), r);
+    r = fma(r, fma(-x, r, 1.0), r);
+    c = (1.0 - t2) * r;
+    s = (2.0 * tau) * r;
+    cm = (-2.0 * t2) * r;
 }
 
 // Shared-memory footprint of a block-pair solve for M = 2b: S, F and a third
@@ -353,79 +367,116 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
 // ---------------------------------------------------------------- mixed precision
 // inner_jacobi for a problem whose S only steers the rotations (the Gram matrix
 // of a one-sided solve: C and V change through W alone).  S is held as an FP64
-// diagonal dg and an FP32 off-diagonal E (both scaled by the same power of two,
-// ld M+1, diagonal entries of E unused); the Rutishauser update moves the
-// diagonal in FP64 (d_p - t e_pq, d_q + t e_pq) and E is rotated in FP32, so
-// the rounding of E is relative to the off-diagonal entries themselves.  The
-// rotations (Lemma 5.1 on the Gram matrix, Lemma 3.1 form) are formed in FP64
-// from dg and E (the tangent in FP32, rotation_cs_mixed) and F = W - I is
-// accumulated in FP64 as in inner_jacobi, so W stays orthogonal to working
-// precision; FP32 rounding in E and t only perturbs the angles (a convergence
-// effect).  csf holds FP32 copies of (c, s) of the two
-// step buffers (4 (M/2) floats).
+// diagonal dg (with an FP32 copy dgf for the threshold test) and an FP32
+// off-diagonal E (both scaled by the same power of two, ld M+1, diagonal
+// entries of E unused); the Rutishauser update moves the diagonal in FP64
+// (d_p - t e_pq, d_q + t e_pq) and E is rotated in FP32, so the rounding of E
+// is relative to the off-diagonal entries themselves.  The angles are formed in
+// FP32 (rotation_angle_mixed), and F = W - I is accumulated in FP64 with the
+// FP64 rotations of the same half-angle tangents (rotation_from_tau), so W
+// stays orthogonal to working precision; FP32 rounding in E and in the angles
+// only perturbs their effect (a convergence matter).
+//
+// Three-stage software pipeline over the steps k of an inner sweep, two
+// barriers per step:
+//   A_k  all warps: S update with the FP32 rotations of step k;
+//   B_k  warp 0: the FP32 rotations of step k+1 from S;
+//        warp 1: the FP64 (c, s, c - 1) of step k;
+//        other warps: F <- F J + (J - I) with the FP64 rotations of step k-1.
+// So the FP64 work never sits on the chain of dependent steps through S.
 template <int M>
-__device__ __forceinline__ int step_rotations_mixed(const double* dg, const float* E, double* cs, float* csf, int* ip,
-                                                    int r, int cross_round, double eps) {
+struct MixedBufs {
+    static constexpr int P = M / 2, LD = M + 1;
+    static constexpr size_t kOffDg = ((size_t)M * LD * 4 + 7) / 8 * 8;
+    static constexpr size_t kOffDgf = kOffDg + 8 * M;
+    static constexpr size_t kOffRf = kOffDgf + 4 * M;                 // 2 sets of (c, s, t, tau), FP32
+    static constexpr size_t kOffRd = (kOffRf + 2 * 4 * P * 4 + 7) / 8 * 8;   // 2 sets of (c, s, c - 1), FP64
+    static constexpr size_t kOffIp = kOffRd + 2 * 3 * P * 8;          // 3 sets of (p, q, skip)
+    static constexpr size_t bytes = kOffIp + 3 * 3 * P * 4;
+    float* E;
+    double* dg;
+    float* dgf;
+    float* rf;
+    double* rd;
+    int* ip;
+    __device__ explicit MixedBufs(unsigned char* base)
+        : E(reinterpret_cast<float*>(base)), dg(reinterpret_cast<double*>(base + kOffDg)),
+          dgf(reinterpret_cast<float*>(base + kOffDgf)), rf(reinterpret_cast<float*>(base + kOffRf)),
+          rd(reinterpret_cast<double*>(base + kOffRd)), ip(reinterpret_cast<int*>(base + kOffIp)) {}
+};
+
+// FP32 rotations of step r (warp 0; lane a < P takes pair a) into one rf set
+// (c, s, t, tau) and one ip set (p, q, skip).  Returns the number of
+// rotations of the step (all lanes of warp 0).
+template <int M>
+__device__ __forceinline__ int step_angles_mixed(const MixedBufs<M>& b, float* rf, int* ipw, int r, int cross_round,
+                                                 float eps) {
     constexpr int LD = M + 1;
     constexpr int P = M / 2;
-    const int tid = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     int mine = 0;
-    if (tid < P) {
+    if (lane < P) {
         int p, q;
         if (cross_round < 0) {
-            p = rr_index(r, tid, M);
-            q = rr_index(r, M - 1 - tid, M);
+            p = rr_index(r, lane, M);
+            q = rr_index(r, M - 1 - lane, M);
         } else if (r < P) {
-            p = tid;
-            q = P + (tid + r) % P;
+            p = lane;
+            q = P + (lane + r) % P;
         } else {
-            const int qr = cross_round % (P - 1), h = tid / (P / 2), i = tid % (P / 2);
+            const int qr = cross_round % (P - 1), h = lane / (P / 2), i = lane % (P / 2);
             p = h * P + rr_index(qr, i, P);
             q = h * P + rr_index(qr, P - 1 - i, P);
         }
         if (p > q) { int t = p; p = q; q = t; }
-        const float ef = E[q * LD + p];
-        const double apq = (double)ef, app = dg[p], aqq = dg[q];
-        double c = 1.0, s = 0.0, t = 0.0, cm = 0.0;
+        const float ef = b.E[q * LD + p];
+        float c = 1.f, s = 0.f, t = 0.f, tau = 0.f;
         int skip = 1;
-        // |s_pq| > eps sqrt(|s_pp s_qq|) as squares (the scaled entries are at most 2)
-        if (ef != 0.f && apq * apq > (eps * eps) * rabs(app * aqq)) {
-            rotation_cs_mixed(app, aqq, ef, c, s, cm, t);
+        // |s_pq| > eps sqrt(s_pp s_qq) in FP32 on the FP32 copies of the diagonal
+        // (scaled to at most 2 and at least 2^-76: the products stay normal)
+        if (ef != 0.f && fabsf(ef) > eps * (sqrtf(fabsf(b.dgf[p])) * sqrtf(fabsf(b.dgf[q])))) {
+            rotation_angle_mixed(b.dg[p], b.dg[q], ef, t, tau);
+            const float r1 = 1.0f / fmaf(tau, tau, 1.0f);
+            c = fmaf(-tau, tau, 1.0f) * r1;
+            s = (2.0f * tau) * r1;
             skip = 0;
         }
-        cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = cm; cs[3 * P + tid] = t;
-        csf[tid] = (float)c; csf[P + tid] = (float)s;
-        ip[tid] = p; ip[P + tid] = q; ip[2 * P + tid] = skip;
+        rf[lane] = c; rf[P + lane] = s; rf[2 * P + lane] = t; rf[3 * P + lane] = tau;
+        ipw[lane] = p; ipw[P + lane] = q; ipw[2 * P + lane] = skip;
         mine = !skip;
     }
     return __popc(__ballot_sync(0xffffffffu, mine));
 }
 
+// S update of one step: the FP64 diagonal (Rutishauser, with the step's t) and
+// the FP32 2 x 2 blocks of E, as step_update_s.
 template <int M>
-__device__ __forceinline__ void step_update_s_mixed(double* dg, float* E, const double* cs, const float* csf,
-                                                    const int* ip, const int (&items)[3]) {
+__device__ __forceinline__ void step_update_s_mixed(const MixedBufs<M>& b, const float* rf, const int* ipr,
+                                                    const int (&items)[3]) {
     constexpr int LD = M + 1;
     constexpr int P = M / 2;
-    const double* tt = cs + 3 * P;
-    const float* snf = csf + P;
-    const int* iq = ip + P;
-    const int* sk = ip + 2 * P;
+    float* E = b.E;
+    const int* iq = ipr + P;
+    const int* sk = ipr + 2 * P;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         if (items[k] < 0) continue;
-        const int a = items[k] & 255, b = items[k] >> 8;
-        const int pa = ip[a], qa = iq[a];
-        if (a == b) {
+        const int a = items[k] & 255, bb = items[k] >> 8;
+        const int pa = ipr[a], qa = iq[a];
+        if (a == bb) {
             // a skipped pair (t = 0) keeps its diagonal and loses its entry, as in inner_jacobi
-            const double apq = (double)E[qa * LD + pa], ta = tt[a];
-            dg[pa] = dg[pa] - ta * apq;
-            dg[qa] = dg[qa] + ta * apq;
+            const double apq = (double)E[qa * LD + pa], ta = (double)rf[2 * P + a];
+            const double dp = fma(-ta, apq, b.dg[pa]), dq = fma(ta, apq, b.dg[qa]);
+            b.dg[pa] = dp;
+            b.dg[qa] = dq;
+            b.dgf[pa] = (float)dp;
+            b.dgf[qa] = (float)dq;
             E[qa * LD + pa] = 0.f;
             E[pa * LD + qa] = 0.f;
         } else {
-            if (sk[a] && sk[b]) continue;
-            const int pb = ip[b], qb = iq[b];
-            const float ca = csf[a], sa = snf[a], cb = csf[b], sb = snf[b];
+            if (sk[a] && sk[bb]) continue;
+            const int pb = ipr[bb], qb = iq[bb];
+            const float ca = rf[a], sa = rf[P + a], cb = rf[bb], sb = rf[P + bb];
             const float x00 = E[pb * LD + pa], x01 = E[qb * LD + pa];
             const float x10 = E[pb * LD + qa], x11 = E[qb * LD + qa];
             const float y00 = ca * x00 - sa * x10, y01 = ca * x01 - sa * x11;
@@ -440,45 +491,60 @@ __device__ __forceinline__ void step_update_s_mixed(double* dg, float* E, const 
     }
 }
 
-// Same schedule, counting and stopping rule as inner_jacobi (tau = 0).  With
-// nrows < M only rows [row0, row0 + nrows) of F are accumulated (the other CTAs
-// of a cluster, which form the same rotations, hold the rest).
+// F update of one step with its FP64 rotations (rd set) on rows
+// [row0, row0 + nrows), by threads t0, t0 + nt, ...
 template <int M>
-__device__ int inner_jacobi_mixed(double* dg, float* E, double* F, double* cs, float* csf, int* ip, double eps,
-                                  int max_inner, int cross_round = -1, int row0 = 0, int nrows = M) {
+__device__ __forceinline__ void step_f_mixed(double* F, const double* rdr, const int* ipr, int t0, int nt, int row0,
+                                             int nrows) {
+    if (nrows != M) step_update_f_rows<double, M>(F, rdr, ipr, t0, nt, row0, nrows);
+    else step_update_f<double, M>(F, rdr, ipr, t0, nt);
+}
+
+// Same schedule, counting and stopping rule as inner_jacobi (tau = 0); the
+// caller has filled b.E, b.dg and b.dgf.  With nrows < M only rows
+// [row0, row0 + nrows) of F are accumulated (the other CTAs of a cluster, which
+// form the same rotations, hold the rest).  cnt: one int of shared scratch.
+template <int M>
+__device__ int inner_jacobi_mixed(const MixedBufs<M>& b, double* F, volatile int* cnt, float eps, int max_inner,
+                                  int cross_round = -1, int row0 = 0, int nrows = M) {
     constexpr int P = M / 2;
     static_assert(P <= 32, "pair count must fit one warp");
-    volatile int* cnt = ip + 6 * P;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int nt = (int)blockDim.x;
     const int nsteps = cross_round >= 0 ? P + 1 : M - 1;
     int items[3];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) items[k] = upper_item<P>(tid + k * (int)blockDim.x);
+    for (int k = 0; k < 3; ++k) items[k] = upper_item<P>(tid + k * nt);
     int total = 0;
     for (int sweep = 0; sweep < max_inner; ++sweep) {
         int applied = 0;
-        if (tid < 32) applied += step_rotations_mixed<M>(dg, E, cs, csf, ip, 0, cross_round, eps);
+        if (warp == 0) applied += step_angles_mixed<M>(b, b.rf, b.ip, 0, cross_round, eps);
         __syncthreads();
-        for (int r = 0; r < nsteps; ++r) {
-            const int cur = r & 1;
-            const double* csc = cs + cur * 4 * P;
-            const float* csfc = csf + cur * 2 * P;
-            const int* ipc = ip + cur * 3 * P;
-            step_update_s_mixed<M>(dg, E, csc, csfc, ipc, items);
+        for (int k = 0; k < nsteps; ++k) {
+            const float* rfk = b.rf + (k & 1) * 4 * P;
+            const int* ipk = b.ip + (k % 3) * 3 * P;
+            step_update_s_mixed<M>(b, rfk, ipk, items);
             __syncthreads();
-            const bool more = r + 1 < nsteps;
-            if (more && tid < 32)
-                applied += step_rotations_mixed<M>(dg, E, cs + (cur ^ 1) * 4 * P, csf + (cur ^ 1) * 2 * P,
-                                                   ip + (cur ^ 1) * 3 * P, r + 1, cross_round, eps);
-            else if (nrows != M)
-                step_update_f_rows<double, M>(F, csc, ipc, more ? tid - 32 : tid,
-                                              more ? blockDim.x - 32 : blockDim.x, row0, nrows);
-            else if (more)
-                step_update_f<double, M>(F, csc, ipc, tid - 32, blockDim.x - 32);
-            else
-                step_update_f<double, M>(F, csc, ipc, tid, blockDim.x);
+            if (warp == 0) {
+                if (k + 1 < nsteps)
+                    applied += step_angles_mixed<M>(b, b.rf + ((k + 1) & 1) * 4 * P, b.ip + ((k + 1) % 3) * 3 * P,
+                                                    k + 1, cross_round, eps);
+            } else if (warp == 1) {
+                const int a = tid & 31;
+                if (a < P) {
+                    double c = 1.0, s = 0.0, cm = 0.0;
+                    if (!ipk[2 * P + a]) rotation_from_tau(rfk[3 * P + a], c, s, cm);
+                    double* rdk = b.rd + (k & 1) * 3 * P;
+                    rdk[a] = c; rdk[P + a] = s; rdk[2 * P + a] = cm;
+                }
+            } else if (k >= 1) {
+                step_f_mixed<M>(F, b.rd + ((k - 1) & 1) * 3 * P, b.ip + ((k - 1) % 3) * 3 * P, tid - 64, nt - 64,
+                                row0, nrows);
+            }
             __syncthreads();
         }
+        step_f_mixed<M>(F, b.rd + ((nsteps - 1) & 1) * 3 * P, b.ip + ((nsteps - 1) % 3) * 3 * P, tid, nt, row0,
+                        nrows);
         if (tid == 0) cnt[0] = applied;
         __syncthreads();
         const int c = cnt[0];

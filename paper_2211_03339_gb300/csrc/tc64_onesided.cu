@@ -415,17 +415,17 @@ k_solve1_tc64(const long long* __restrict__ Ghi, const long long* __restrict__ G
             v[i] = S[(q / kM) * LD + q % kM] * sc;
         }
         __syncthreads();
-        float* E = reinterpret_cast<float*>(S);                       // M x (M+1) floats
-        double* dg = reinterpret_cast<double*>(E + kM * LD);          // then M doubles
-        float* csf = reinterpret_cast<float*>(dg + kM);               // then 4 (M/2) floats
+        const MixedBufs<kM> mb(reinterpret_cast<unsigned char*>(S));
+        static_assert(MixedBufs<kM>::bytes <= sizeof(double) * kM * LD, "mixed buffers fit in S");
 #pragma unroll
         for (int i = 0; i < kM * kM / kSolveThreads; ++i) {
             const int q = t + kSolveThreads * i, r = q % kM, c = q / kM;
-            E[c * LD + r] = (float)v[i];
-            if (r == c) dg[r] = v[i];
+            mb.E[c * LD + r] = (float)v[i];
+            if (r == c) { mb.dg[r] = v[i]; mb.dgf[r] = (float)v[i]; }
         }
         __syncthreads();
-        applied = inner_jacobi_mixed<kM>(dg, E, F, cs, csf, ip, tol_rot, max_inner, cross_round, row0, nrows);
+        applied = inner_jacobi_mixed<kM>(mb, F, ip + 6 * (kM / 2), (float)tol_rot, max_inner, cross_round, row0,
+                                         nrows);
     } else {
         applied = inner_jacobi<double, kM>(S, F, cs, ip, tol_rot, 0.0, max_inner, cross_round, row0, nrows);
     }
