@@ -54,7 +54,10 @@ def parse():
                     help="skip the other workloads (spectra, orders 1024-8192, SVD shapes)")
     ap.add_argument("--batch", type=int, default=10000, help="matrices in the batched workload")
     ap.add_argument("--once", action="store_true",
-                    help="run one mpj_syevj_mp solve and exit (for profiler captures)")
+                    help="run one mpj_syevj_mp solve (or, with --svd, one mpj_gesvj_mp) and exit "
+                         "(for profiler captures)")
+    ap.add_argument("--svd", default=None, metavar="MxN",
+                    help="with --once: the SVD workload of that shape (sigma geometric from 1 to 1e-10)")
     ap.add_argument("--study", choices=["ex2", "svd", "precision"],
                     help="print one JSON line per case of a sweep-count study instead of the "
                          "benchmark line: ex2 = multiple eigenvalues (Example 2, n = 2048/4096, "
@@ -131,10 +134,11 @@ def measured_bf16():
         return 1900.0, "fallback 1.9 PFLOP/s bf16"
 
 
-def source_sha():
+def source_sha(files):
+    """Hash of the named kernel sources (paper_2211_03339_gb300/csrc), in order."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2211_03339_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in files:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(f.encode()); h.update(fh.read())
     return h.hexdigest()[:16]
@@ -142,15 +146,21 @@ def source_sha():
 
 def profiled_traffic(n, kclass):
     """DRAM bytes per launch of a kernel class from its committed ncu summary
-    (profiles/<class>_n<n>.md), if it was taken on the current kernel sources
-    (else None)."""
+    (profiles/<class>_n<n>.md), if the sources it lists ("sources: a.cu b.cuh")
+    still hash to the recorded source_sha (else None: the kernel has changed)."""
     try:
         txt = open(os.path.join(PROFILE_DIR, f"{kclass}_n{n}.md")).read()
     except OSError:
         return None
+    m0 = re.search(r"^sources:\s*(.+)$", txt, re.M)
     m1 = re.search(r"source_sha:\s*([0-9a-f]+)", txt)
     m2 = re.search(r"traffic_bytes_per_launch_n%d:\s*([0-9.eE+]+)" % n, txt)
-    if not m1 or not m2 or m1.group(1) != source_sha():
+    if not m0 or not m1 or not m2:
+        return None
+    try:
+        if m1.group(1) != source_sha(m0.group(1).split()):
+            return None
+    except OSError:
         return None
     return float(m2.group(1))
 
@@ -350,11 +360,20 @@ def run_extras(args, dev):
             oru = torch.linalg.matrix_norm(Uo.T @ Uo - I).item()
             orv = torch.linalg.matrix_norm(V.T @ V - I).item()
             Sn = S.cpu().numpy()
+            # one more run with every launch timed on its stream: the kernel breakdown
+            mpj.profile_reset()
+            mpj.profile_enable(True)
+            fn(A, options={"max_sweeps": 80})
+            torch.cuda.synchronize(dev)
+            mpj.profile_enable(False)
+            prof = mpj.profile_read()
             entry[name] = {"ms": ms, "sweeps": st["sweeps"], "sweeps_stage1": st["sweeps_stage1"],
                            "JU_over_N": st["rotations"], "stages_ms": st["ms_stage"],
                            "res_over_nu": res / (n * U), "orthU_over_nu": oru / (n * U),
                            "orthV_over_nu": orv / (n * U),
-                           "sigma_err_over_nu_s1": float(np.max(np.abs(Sn - sig))) / (n * U * sig[0])}
+                           "sigma_err_over_nu_s1": float(np.max(np.abs(Sn - sig))) / (n * U * sig[0]),
+                           "sigma_relerr_max": float(np.max(np.abs(Sn - sig) / sig)),
+                           "kernels_ms": {k: round(v[1], 1) for k, v in prof.items() if v[0]}}
             del S, Uo, V
         entry["speedup_mp_over_plain"] = entry["plain"]["ms"] / entry["mp"]["ms"]
         out[f"gesvj_{m}x{n}"] = entry
@@ -712,6 +731,13 @@ def run_once(args):
     __graft_entry__.build()
     import paper_2211_03339_gb300 as mpj
     from paper_2211_03339_gb300 import synth
+    if args.svd:
+        m, n = (int(x) for x in args.svd.lower().split("x"))
+        A_np, _, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, 0), sigma_min=1e-10)
+        S, U_, V, st = mpj.gesvj_mp(torch.from_numpy(A_np).cuda())
+        torch.cuda.synchronize()
+        print(json.dumps({"once": True, "m": m, "n": n, "stats": st}))
+        return 0
     A_np, _ = synth.sym_matrix(args.n, args.spectrum, seed=synth_seed(0))
     L, V, st = mpj.syevj_mp(torch.from_numpy(A_np).cuda())
     torch.cuda.synchronize()
