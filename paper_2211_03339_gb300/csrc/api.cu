@@ -304,7 +304,8 @@ int svd_layout(Arena& a, int m, int n, int N, int B, bool mp, SvdBufs& b) {
     b.V32 = mp ? a.take<float>(NN) : nullptr;
     b.eng = a.take<char>(max2(max2(onesided_workspace_bytes<double>(m, N, B),
                                    onesided_workspace_bytes<float>(m, N, B)),
-                              onesided_tc64_supported(m, N, B) ? onesided_tc64_workspace_bytes(m, N) : 0));
+                              max2(onesided_tc64_supported(m, N, B) ? onesided_tc64_workspace_bytes(m, N) : 0,
+                                   onesided_tc32_supported(m, N, B) ? onesided_tc32_workspace_bytes(m, N) : 0)));
     b.mgsw = mp ? a.take<char>(mgs_workspace_bytes(n, n)) : nullptr;
     b.ozA = mp ? a.take<char>(oz_operand_bytes(m, n)) : nullptr;
     b.ozQ = mp ? a.take<char>(oz_operand_bytes(n, n)) : nullptr;
@@ -359,13 +360,24 @@ int gesvj_impl(bool mp, const double* A, int m, int n, int lda, double* Sigma, d
     SweepResult r1, r2;
     if (mp) {
         // step 1: one-sided FP32 Jacobi of fl32(A); Z = right vectors ordered by decreasing ||c_j||
-        MPJ_TRY(copy_pad_f32(A, lda, m, n, b.C32, m, m, N, false, s));
-        MPJ_TRY(set_identity_f32(b.V32, N, N, N, s));
-        MPJ_TRY(onesided_sweeps<float>(b.C32, m, b.V32, m, N, n, B, sqrt((double)m) * kUps,
-                                       op.ju_ratio, op.max_sweeps1, op.max_inner, b.eng, s, &r1));
-        MPJ_TRY(colnorms2_f32(b.C32, m, m, n, b.sc.d, s));
-        MPJ_TRY(rank_sort(b.sc.d, 1, n, true, b.sc.perm, s));
-        MPJ_TRY(gather_z32(b.V32, N, b.sc.perm, n, b.Q, n, s));
+        if (!knobs().simt_stage1 && onesided_tc32_supported(m, N, B)) {
+            // TF32 tensor cores: C and V row-major (the rotations' operands K-major)
+            MPJ_TRY(copy_rowmajor_f32(A, lda, m, n, b.C32, N, s));
+            MPJ_TRY(set_identity_f32(b.V32, N, N, N, s));
+            MPJ_TRY(onesided_sweeps_tc32(b.C32, b.V32, m, N, n, sqrt((double)m) * kUps, op.ju_ratio,
+                                         op.max_sweeps1, op.max_inner, b.eng, s, &r1));
+            MPJ_TRY(colnorms2_rowmajor_f32(b.C32, m, N, n, b.sc.d, s));
+            MPJ_TRY(rank_sort(b.sc.d, 1, n, true, b.sc.perm, s));
+            MPJ_TRY(gather_z32_rowmajor(b.V32, N, b.sc.perm, n, b.Q, n, s));
+        } else {
+            MPJ_TRY(copy_pad_f32(A, lda, m, n, b.C32, m, m, N, false, s));
+            MPJ_TRY(set_identity_f32(b.V32, N, N, N, s));
+            MPJ_TRY(onesided_sweeps<float>(b.C32, m, b.V32, m, N, n, B, sqrt((double)m) * kUps,
+                                           op.ju_ratio, op.max_sweeps1, op.max_inner, b.eng, s, &r1));
+            MPJ_TRY(colnorms2_f32(b.C32, m, m, n, b.sc.d, s));
+            MPJ_TRY(rank_sort(b.sc.d, 1, n, true, b.sc.perm, s));
+            MPJ_TRY(gather_z32(b.V32, N, b.sc.perm, n, b.Q, n, s));
+        }
         tm.mark(1);
         if (n >= 1024 && oz_enabled() && oz_supported(n, n, n)) {                           // step 2
             MPJ_TRY(mgs_blocked_oz(b.Q, n, n, n, b.mgsw, b.sc.flag, b.ozA, b.ozs, b.Rbuf, s));

@@ -171,6 +171,21 @@ bool onesided_tc64_supported(int m, int N, int B);
 size_t onesided_tc64_workspace_bytes(int m, int N);
 int onesided_sweeps_tc64(double* C, double* V, int m, int N, int n, double tol_rot, double ju_ratio,
                          int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res);
+// One-sided FP32 sweeps (step 1 of Alg. 5.2) with the block Grams and rotations
+// on the TF32 tensor cores (tc_apply.cu): C (m x N) and V (N x N) row-major,
+// b = 32, N a multiple of 64, m >= 128.  The block solves are the SIMT FP32
+// solves of onesided.cu (solve1_f32_round).
+bool onesided_tc32_supported(int m, int N, int B);
+size_t onesided_tc32_workspace_bytes(int m, int N);
+int onesided_sweeps_tc32(float* C, float* V, int m, int N, int n, double tol_rot, double ju_ratio,
+                         int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res);
+int configure_solve1_f32();
+int solve1_f32_round(const float* Ghi, const float* Glo, int nsplit, int K, float* Wbuf, double tol_rot,
+                     int max_inner, int cross_round, unsigned long long* rot, cudaStream_t s);
+// Row-major FP32 copy of A (m x n, padded with zero columns to N) and the squared
+// column norms of a row-major C.
+int copy_rowmajor_f32(const double* A, int lda, int m, int n, float* C, int N, cudaStream_t s);
+int colnorms2_rowmajor_f32(const float* C, int m, int N, int n, double* nrm2, cudaStream_t s);
 // Z[:, c] = V[:, perm[c]] (widened) from a row-major V.
 int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double* Z, int ldz,
                         cudaStream_t s);

@@ -308,6 +308,20 @@ int onesided_sweeps(Real* C, int ldc, Real* V, int m, int N, int n, int B, doubl
     return MPJ_SUCCESS;
 }
 
+// The FP32 block solves of one round (b = 32) on Gram partials formed by the
+// caller -- the tensor-core step 1 of Alg. 5.2 (tc_apply.cu): W_b - I to Wbuf.
+int configure_solve1_f32() { return configure_onesided<float, 32>(); }
+int solve1_f32_round(const float* Ghi, const float* Glo, int nsplit, int K, float* Wbuf, double tol_rot,
+                     int max_inner, int cross_round, unsigned long long* rot, cudaStream_t s) {
+    {
+        MPJ_PROF(PC_SOLVE1_F32, s);
+        k_solve1<float, 32><<<K, kSolveThreads, InnerLayout<float, 64>::bytes, s>>>(
+            Ghi, Glo, nsplit, Wbuf, (float)tol_rot, 1.0f / 4096.0f, max_inner, cross_round, rot);
+    }
+    MPJ_LAUNCH_CHECK("k_solve1<float>");
+    return MPJ_SUCCESS;
+}
+
 template size_t onesided_workspace_bytes<float>(int, int, int);
 template size_t onesided_workspace_bytes<double>(int, int, int);
 template int onesided_sweeps<float>(float*, int, float*, int, int, int, int, double, double, int,

@@ -261,6 +261,204 @@ k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N
     if (warp == 0) tc::tmem_dealloc(tmem, kM);
 }
 
+// ---------------------------------------------------------------- one-sided FP32
+// Step 1 of Algorithm 5.2 on the tensor cores: C (m x N) and V (N x N) are kept
+// row-major, so that the block rotations C_IJ <- C_IJ W_b and V_IJ <- V_IJ W_b
+// are the V-type items of k_pass_tc (a row slab times W_b, stored back by TMA).
+// The block Grams G_b = C_IJ^T C_IJ contract over the rows of C: k_gram_tc32
+// loads chunks of 32 rows of the pair's 64 columns by TMA, transposes them in
+// shared memory into the TF32 hi / lo planes of C_IJ^T (64 rows, K-major,
+// 128-byte swizzle), and accumulates hi hi^T + hi lo^T (one MMA with N = 128
+// over the hi and lo planes) and lo hi^T (N = 64) in FP32 in TMEM: about FP32
+// accuracy, like the SIMT FP32 Gram it replaces.  M = 64 (the pair's columns):
+// row i of the accumulator sits in TMEM lane 32 (i / 16) + i % 16.
+constexpr int kG32Thr = 128;
+constexpr int kG32Stage = 2 * 32 * 32;               // floats: two TMA boxes of 32 rows x 32 columns
+constexpr int kG32Plane = kM * 32;                   // floats: 64 pair columns x 32 rows of C
+constexpr int kG32Slot = 2 * kG32Plane;              // hi and lo planes, one after the other
+constexpr size_t kGram32Smem = sizeof(float) * (size_t)(2 * kG32Stage + 2 * kG32Slot) + 1024;
+constexpr int kGram32Ctas = 304;                     // target CTAs of a Gram launch (two per SM)
+
+// One CTA per (pair b, row range); the partial Gram of its rows to
+// Ghi[(b nsplit + split) M^2 + c M + r] (Glo = 0), the layout the FP32 block
+// solves sum.  Bounded waits; a timeout sets *err.
+__global__ void __launch_bounds__(kG32Thr, 2)
+k_gram_tc32(const __grid_constant__ CUtensorMap map, int m, int N, int round, int rows_per,
+            float* __restrict__ Ghi, float* __restrict__ Glo, unsigned long long* __restrict__ err) {
+    extern __shared__ unsigned char smraw[];
+    float* sm = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    float* Xs = sm;                                  // two load stages
+    float* Ps = sm + 2 * kG32Stage;                  // two plane slots
+    __shared__ __align__(8) uint64_t xfull[2], mdone[2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.x, split = blockIdx.y, nsplit = gridDim.y;
+    int I, J;
+    round_pair(round, b, N / kB, I, J);
+    const int r0 = split * rows_per;
+    const int r1 = min(m, r0 + rows_per);
+    const int nq = (r1 - r0 + 31) / 32;
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) { tc::mbar_init(&xfull[i], 1); tc::mbar_init(&mdone[i], 1); }
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, 256);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    auto load = [&](int q) {
+        const int st = q & 1;
+        tc::mbar_expect_tx(&xfull[st], sizeof(float) * kG32Stage);
+        tc::tma_load_2d(Xs + st * kG32Stage, &map, I * kB, r0 + 32 * q, &xfull[st]);
+        tc::tma_load_2d(Xs + st * kG32Stage + 1024, &map, J * kB, r0 + 32 * q, &xfull[st]);
+    };
+    if (tid == 0)
+        for (int q = 0; q < nq && q < 2; ++q) load(q);
+    bool ok = true;
+    constexpr uint32_t idesc1 = tc::instr_desc(tc::kFmtTF32, kM, 2 * kM);
+    constexpr uint32_t idesc2 = tc::instr_desc(tc::kFmtTF32, kM, kM);
+    for (int q = 0; q < nq; ++q) {
+        const int st = q & 1;
+        ok = tc::mbar_wait(&xfull[st], (q >> 1) & 1, kTcWait) && ok;
+        if (q >= 2) ok = tc::mbar_wait(&mdone[st], ((q >> 1) - 1) & 1, kTcWait) && ok;
+        {
+            // thread (4-row group rb, 4-column group cb): a 4 x 4 block transposed
+            // through registers, split into TF32 hi and lo
+            const float* X = Xs + st * kG32Stage;
+            float* H = Ps + st * kG32Slot;
+            float* L = H + kG32Plane;
+            const int rb = tid >> 4, cb = tid & 15;
+            const float* Xb = X + (cb >> 3) * 1024;
+            const int cc = cb & 7;
+            float v[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * rb + i;
+                const float4 x = *reinterpret_cast<const float4*>(Xb + r * 32 + ((cc ^ (r & 7)) << 2));
+                v[i][0] = x.x; v[i][1] = x.y; v[i][2] = x.z; v[i][3] = x.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = 4 * cb + j;
+                float4 h, l;
+                tc::split_tf32(v[0][j], h.x, l.x);
+                tc::split_tf32(v[1][j], h.y, l.y);
+                tc::split_tf32(v[2][j], h.z, l.z);
+                tc::split_tf32(v[3][j], h.w, l.w);
+                const int off = tc::sw128_off(c, rb);
+                *reinterpret_cast<float4*>(H + off) = h;
+                *reinterpret_cast<float4*>(L + off) = l;
+            }
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();                             // stage st read, planes of slot st written
+        tc::fence_after_sync();
+        if (tid == 0) {
+            if (q + 2 < nq) load(q + 2);
+            if (ok) {
+                const uint32_t h0 = tc::smem_u32(Ps + st * kG32Slot);
+                const uint32_t l0 = h0 + sizeof(float) * kG32Plane;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {     // K = 8 per MMA: 32 bytes along the 128-byte row
+                    const uint32_t acc = (q > 0 || ks > 0) ? 1u : 0u;
+                    // [hi hi^T | hi lo^T]: the hi and lo planes form one 128-row operand
+                    tc::mma_tf32(tmem, tc::smem_desc_sw128(h0 + ks * 32), tc::smem_desc_sw128(h0 + ks * 32),
+                                 idesc1, acc);
+                    tc::mma_tf32(tmem + 2 * kM, tc::smem_desc_sw128(l0 + ks * 32),
+                                 tc::smem_desc_sw128(h0 + ks * 32), idesc2, acc);
+                }
+            }
+            tc::commit(&mdone[st]);
+        }
+    }
+    if (nq > 0) ok = tc::mbar_wait(&mdone[(nq - 1) & 1], ((nq - 1) >> 1) & 1, kTcWait) && ok;
+    tc::fence_after_sync();
+    if (ok && nq > 0) {
+        const uint32_t lanebase = tmem + ((uint32_t)(32 * warp) << 16);
+        const int i = 16 * warp + (lane & 15);       // row i of G (lanes 16-31 unused)
+        const size_t base = ((size_t)b * nsplit + split) * kM * kM;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kM; c0 += 16) {
+            float a[16], x[16], y[16];
+            tc::tmem_ld16(lanebase + (uint32_t)c0, a);
+            tc::tmem_ld16(lanebase + (uint32_t)(kM + c0), x);
+            tc::tmem_ld16(lanebase + (uint32_t)(2 * kM + c0), y);
+            tc::tmem_wait_ld();
+            if (lane < 16) {
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    Ghi[base + (size_t)(c0 + jj) * kM + i] = a[jj] + (x[jj] + y[jj]);
+                    Glo[base + (size_t)(c0 + jj) * kM + i] = 0.f;
+                }
+            }
+        }
+    }
+    if (!ok && tid == 0) atomicExch(err, 1ull);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+}
+
+// TF32 hi / lo image of F_b^T (row n, column k: F_b[k][n]) from the block solve's
+// row-major F_b, for the B operand of k_pass_tc, and max |F_b|.
+__global__ void __launch_bounds__(256)
+k_fimg32(const float* __restrict__ Wbuf, float* __restrict__ Fimg, float* __restrict__ fmax) {
+    __shared__ float red[8];
+    const int b = blockIdx.x;
+    const float* F = Wbuf + (size_t)b * kM * kM;
+    float* img = Fimg + (size_t)b * 2 * kM * kM;
+    float mx = 0.f;
+    for (int t = threadIdx.x; t < kM * kM; t += blockDim.x) {
+        const int n = t / kM, k = t % kM;
+        const float v = F[k * kM + n];
+        float h, l;
+        tc::split_tf32(v, h, l);
+        img[t] = h;
+        img[kM * kM + t] = l;
+        mx = fmaxf(mx, fabsf(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = 0.f;
+        for (int w = 0; w < 8; ++w) r = fmaxf(r, red[w]);
+        fmax[b] = r;
+    }
+}
+
+// C[r N + c] = fl32(A[r + c lda]) for c < n, 0 for n <= c < N (row-major, padded).
+__global__ void k_copy_rowmajor_f32(const double* __restrict__ A, int lda, int m, int n, float* __restrict__ C,
+                                    int N) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + threadIdx.x, c = c0 + k;
+        tile[k][threadIdx.x] = (r < m && c < n) ? (float)A[(size_t)r + (size_t)c * lda] : 0.f;
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int r = r0 + k, c = c0 + threadIdx.x;
+        if (r < m && c < N) C[(size_t)r * N + c] = tile[threadIdx.x][k];
+    }
+}
+
+// out[c] += sum over this block's rows of C[r N + c]^2 (row-major C; out zeroed first).
+__global__ void k_colnorms2_rowmajor(const float* __restrict__ C, int m, int N, int n, int rows_per,
+                                     double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    const int r0 = blockIdx.y * rows_per, r1 = min(m, r0 + rows_per);
+    double acc = 0.0;
+    for (int r = r0; r < r1; ++r) {
+        const double v = (double)C[(size_t)r * N + c];
+        acc = fma(v, v, acc);
+    }
+    atomicAdd(out + c, acc);
+}
+
 __global__ void k_gather_z32_rowmajor(const float* __restrict__ Vt, int ld, const int* __restrict__ perm,
                                       int n, double* __restrict__ Z, int ldz) {
     // Z[:, c] = V[:, perm[c]] with V row-major (V[r][p] = Vt[p + r ld]); one row of
@@ -461,6 +659,155 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     if (res->status == MPJ_NOT_CONVERGED && std::isfinite(off) && !(off > tol_abs))
         res->status = MPJ_SUCCESS;
     res->off_final = off;
+    return MPJ_SUCCESS;
+}
+
+// ---------------------------------------------------------------- one-sided FP32 engine
+namespace {
+void gram32_split(int m, int K, int* nsplit, int* rows_per) {
+    const int want = kGram32Ctas / K > 1 ? kGram32Ctas / K : 1;
+    const int chunks = (m + 31) / 32;
+    int per = (chunks + want - 1) / want;
+    if (per < 1) per = 1;
+    *rows_per = per * 32;
+    *nsplit = (m + *rows_per - 1) / *rows_per;
+}
+}  // namespace
+
+bool onesided_tc32_supported(int m, int N, int B) { return B == kB && N % kM == 0 && N >= kM && m >= kSlab; }
+
+size_t onesided_tc32_workspace_bytes(int m, int N) {
+    const size_t K = (size_t)(N / kM);
+    int nsplit = 1, rows_per = 32;
+    if (K > 0) gram32_split(m, (int)K, &nsplit, &rows_per);
+    Arena a;
+    for (int set = 0; set < 2; ++set) {
+        a.take<float>(K * kM * kM);               // W_b - I
+        a.take<float>(K * 2 * kM * kM);           // TF32 image of F_b^T
+        a.take<float>(K);                         // max |F_b|
+    }
+    a.take<float>(K * nsplit * kM * kM);          // Gram partials (hi)
+    a.take<float>(K * nsplit * kM * kM);          //               (lo, zero)
+    a.take<unsigned long long>(4);
+    return a.used + 256;
+}
+
+int onesided_sweeps_tc32(float* C, float* V, int m, int N, int n, double tol_rot, double ju_ratio,
+                         int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res) {
+    if (!onesided_tc32_supported(m, N, kB)) {
+        set_error_msg("tensor-core FP32 one-sided engine: needs b = 32, N a multiple of 64, m >= 128");
+        return MPJ_BAD_ARG;
+    }
+    const int K = N / kM;
+    int nsplit, rows_per;
+    gram32_split(m, K, &nsplit, &rows_per);
+    Arena ar;
+    ar.base = static_cast<char*>(work);
+    ar.size = onesided_tc32_workspace_bytes(m, N);
+    float *Wbuf[2], *Fimg[2], *fmax[2];
+    for (int set = 0; set < 2; ++set) {
+        Wbuf[set] = ar.take<float>((size_t)K * kM * kM);
+        Fimg[set] = ar.take<float>((size_t)K * 2 * kM * kM);
+        fmax[set] = ar.take<float>((size_t)K);
+    }
+    float* Ghi = ar.take<float>((size_t)K * nsplit * kM * kM);
+    float* Glo = ar.take<float>((size_t)K * nsplit * kM * kM);
+    unsigned long long* rot = ar.take<unsigned long long>(4);     // [0] rotations, [1] error flag
+    if (!fmax[1] || !Ghi || !Glo || !rot) { set_error_msg("workspace too small"); return MPJ_BAD_ARG; }
+    HostScratch hs;
+    MPJ_TRY(hs.init());
+    MPJ_TRY(configure_solve1_f32());
+    MPJ_CUDA_TRY(cudaFuncSetAttribute(k_gram_tc32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGram32Smem));
+    MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
+    CUtensorMap mg;
+    MPJ_TRY(encode_rows(&mg, C, N, m, 32));              // Gram: 32 rows x 32 columns per box
+    PassMaps mc[2], mv[2];                               // rotations: row slabs of C and of V
+    for (int set = 0; set < 2; ++set) {
+        MPJ_TRY(encode_rows(&mc[set].v, C, N, m, kSlab));
+        mc[set].in_t = mc[set].v;
+        MPJ_TRY(encode_rows(&mc[set].f, Fimg[set], kM, (uint64_t)K * 2 * kM, kM));
+        MPJ_TRY(encode_rows(&mv[set].v, V, N, N, kSlab));
+        mv[set].in_t = mv[set].v;
+        mv[set].f = mc[set].f;
+    }
+    SideStream side;
+    MPJ_TRY(side.init(s));
+    s = side.main;
+    MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, 2 * sizeof(unsigned long long), s));
+    res->sweeps = 0;
+    res->rotations = 0;
+    res->status = MPJ_NOT_CONVERGED;
+    const int rounds = 2 * K - 1;
+    const int slabsC = (m + kSlab - 1) / kSlab, itemsC = slabsC * K;
+    const int slabsV = (N + kSlab - 1) / kSlab, itemsV = slabsV * K;
+    const int gridC = itemsC < 2 * sm_count() ? itemsC : 2 * sm_count();
+    const int gridV = itemsV < 2 * sm_count() ? itemsV : 2 * sm_count();
+    const double Npairs = 0.5 * (double)n * (double)(n - 1);
+    const bool cross = N >= kB * kB && !knobs().full_inner;
+    while (res->sweeps < max_sweeps) {
+        MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        for (int r = 0; r < rounds; ++r) {
+            const int set = side.begin_round();
+            if (set < 0) return MPJ_CUDA_ERROR;
+            {
+                MPJ_PROF(PC_GRAM1_F32, s);
+                k_gram_tc32<<<dim3(K, nsplit), kG32Thr, kGram32Smem, s>>>(mg, m, N, r, rows_per, Ghi, Glo, rot + 1);
+            }
+            MPJ_LAUNCH_CHECK("k_gram_tc32");
+            MPJ_TRY(solve1_f32_round(Ghi, Glo, nsplit, K, Wbuf[set], tol_rot, max_inner, cross ? r : -1, rot, s));
+            {
+                MPJ_PROF(PC_AUX, s);
+                k_fimg32<<<K, 256, 0, s>>>(Wbuf[set], Fimg[set], fmax[set]);
+            }
+            MPJ_LAUNCH_CHECK("k_fimg32");
+            MPJ_TRY(side.after_solve());
+            {
+                MPJ_PROF(PC_APPLY1_F32, side.sv);
+                k_pass_tc<<<gridV, kTcThreads, kPassSmem, side.sv>>>(mv[set], nullptr, N, slabsV, 0, itemsV, nullptr,
+                                                                     fmax[set], r, 3, rot + 1);
+            }
+            MPJ_LAUNCH_CHECK("k_pass_tc V (one-sided)");
+            MPJ_TRY(side.after_v());
+            {
+                MPJ_PROF(PC_APPLY1_F32, s);
+                k_pass_tc<<<gridC, kTcThreads, kPassSmem, s>>>(mc[set], nullptr, N, slabsC, 0, itemsC, nullptr,
+                                                               fmax[set], r, 3, rot + 1);
+            }
+            MPJ_LAUNCH_CHECK("k_pass_tc C (one-sided)");
+            side.end_round();
+        }
+        MPJ_CUDA_TRY(cudaMemcpyAsync(hs.u, rot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        MPJ_CUDA_TRY(cudaStreamSynchronize(s));
+        prof_flush();
+        if (hs.u[1]) { set_error_msg("tensor-core FP32 one-sided sweep: a wait timed out"); return MPJ_CUDA_ERROR; }
+        res->sweeps += 1;
+        res->rotations += (double)hs.u[0];
+        if (trace_on())
+            fprintf(stderr, "[mpj] onesided<tc32> m=%d n=%d sweep %d: %llu rotations (%.4f N)\n", m, n, res->sweeps,
+                    hs.u[0], hs.u[0] / Npairs);
+        const double applied = (double)hs.u[0];
+        if (hs.u[0] == 0 || applied < ju_ratio * Npairs) { res->status = MPJ_SUCCESS; break; }
+    }
+    return MPJ_SUCCESS;
+}
+
+int copy_rowmajor_f32(const double* A, int lda, int m, int n, float* C, int N, cudaStream_t s) {
+    {
+        MPJ_PROF(PC_AUX, s);
+        k_copy_rowmajor_f32<<<dim3((N + 31) / 32, (m + 31) / 32), dim3(32, 8), 0, s>>>(A, lda, m, n, C, N);
+    }
+    MPJ_LAUNCH_CHECK("k_copy_rowmajor_f32");
+    return MPJ_SUCCESS;
+}
+
+int colnorms2_rowmajor_f32(const float* C, int m, int N, int n, double* nrm2, cudaStream_t s) {
+    MPJ_CUDA_TRY(cudaMemsetAsync(nrm2, 0, sizeof(double) * (size_t)n, s));
+    const int splits = (m + 255) / 256;
+    {
+        MPJ_PROF(PC_AUX, s);
+        k_colnorms2_rowmajor<<<dim3((n + 255) / 256, splits), 256, 0, s>>>(C, m, N, n, 256, nrm2);
+    }
+    MPJ_LAUNCH_CHECK("k_colnorms2_rowmajor");
     return MPJ_SUCCESS;
 }
 

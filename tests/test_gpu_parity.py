@@ -268,12 +268,13 @@ def test_gesvj_tensor_core_sweeps_vs_simt(mpj, method):
     cores (n > 256: b = 32, N = 448, m = 520 rows: four full slabs and a ragged one)
     with the block solves' Gram in FP32/FP64 (default) or all FP64 (MPJ_OPT_FP64_SOLVES),
     and the SIMT engine (MPJ_OPT_SIMT_SWEEPS) on the same matrix, all against the
-    oracle's singular values."""
+    oracle's singular values; step 1 on the TF32 tensor cores (default) and on the
+    SIMT FP32 engine (MPJ_OPT_SIMT_STAGE1)."""
     m, n = 520, 448
     A, sig, _, _ = synth.svd_matrix(m, n, seed=synth.seed_for(2, 7), sigma_min=1e-10)
     So = _oracle_sigma_520x448()
     f = mpj.gesvj_mp if method == "mp" else mpj.gesvj_plain
-    for flags in (0, mpj.OPT_FP64_SOLVES, mpj.OPT_SIMT_SWEEPS):
+    for flags in (0, mpj.OPT_FP64_SOLVES, mpj.OPT_SIMT_SWEEPS, mpj.OPT_SIMT_STAGE1):
         Sg, Ug, Vg, st = f(dev(A), options={"flags": flags, "max_sweeps": 100})
         Sg, Ug, Vg = host(Sg), host(Ug), host(Vg)
         assert (np.diff(Sg) <= 0).all()
