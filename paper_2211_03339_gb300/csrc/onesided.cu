@@ -119,8 +119,14 @@ k_gram1(const Real* __restrict__ C, size_t ldc, int m, int N, int round, int row
         }
 }
 
+// Threads of a block solve: FP32 solves are chains of short dependent steps
+// (more warps hide more of their latency, as in the FP32 two-sided solves);
+// FP64 solves are bound by the FP64 pipe.
+template <class Real>
+constexpr int solve1_threads() { return sizeof(Real) == 4 ? 1024 : kSolveThreads; }
+
 template <class Real, int B>
-__global__ void __launch_bounds__(kSolveThreads)
+__global__ void __launch_bounds__(solve1_threads<Real>())
 k_solve1(const Real* __restrict__ Ghi, const Real* __restrict__ Glo, int nsplit,
          Real* __restrict__ Fbuf, Real tol_rot,
          Real gate, int max_inner, int cross_round, unsigned long long* __restrict__ rot_counter) {
@@ -225,7 +231,7 @@ static int launch_round1(Real* C, int ldc, Real* V, int m, int N, Real* Wbuf, Re
     k_gram1<Real, B><<<g, kThreads, 0, s>>>(C, (size_t)ldc, m, N, r, rows_per, Ghi, Glo, nsplit, comp); }
     MPJ_LAUNCH_CHECK("k_gram1");
     { MPJ_PROF(sizeof(Real) == 8 ? PC_SOLVE1_F64 : PC_SOLVE1_F32, s);
-    k_solve1<Real, B><<<K, kSolveThreads, InnerLayout<Real, M>::bytes, s>>>(Ghi, Glo, nsplit, Wbuf, tol_rot,
+    k_solve1<Real, B><<<K, solve1_threads<Real>(), InnerLayout<Real, M>::bytes, s>>>(Ghi, Glo, nsplit, Wbuf, tol_rot,
                                                                       gate, max_inner, cross ? r : -1, rot); }
     MPJ_LAUNCH_CHECK("k_solve1");
     int n_ctiles = ((m + M - 1) / M) * K;
@@ -315,7 +321,7 @@ int solve1_f32_round(const float* Ghi, const float* Glo, int nsplit, int K, floa
                      int max_inner, int cross_round, unsigned long long* rot, cudaStream_t s) {
     {
         MPJ_PROF(PC_SOLVE1_F32, s);
-        k_solve1<float, 32><<<K, kSolveThreads, InnerLayout<float, 64>::bytes, s>>>(
+        k_solve1<float, 32><<<K, solve1_threads<float>(), InnerLayout<float, 64>::bytes, s>>>(
             Ghi, Glo, nsplit, Wbuf, (float)tol_rot, 1.0f / 4096.0f, max_inner, cross_round, rot);
     }
     MPJ_LAUNCH_CHECK("k_solve1<float>");
