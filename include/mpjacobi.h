@@ -285,6 +285,12 @@ void mpj_profile_enable(int on);
 void mpj_profile_reset(void);
 /* launches and summed event time (ms) of class kclass (0 <= kclass < classes) */
 int mpj_profile_read(int kclass, long long* launches, double* total_ms);
+/* Algorithmic bytes that the library itself counted for the launches of class
+ * kclass since the last reset (0 for classes that count none): the one-pass
+ * tile update of the FP32 step counts 3 x 64 x 64 x 4 bytes per off-diagonal
+ * tile it updates (read once, written with its mirror); tiles whose two block
+ * rotations are the identity are skipped and not counted. */
+int mpj_profile_units(int kclass, double* bytes);
 const char* mpj_profile_name(int kclass);
 int mpj_profile_classes(void);
 unsigned long long mpj_kernel_launches(void);   /* all classes, since load */

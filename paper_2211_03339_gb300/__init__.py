@@ -38,7 +38,7 @@ EXPORTS = ["mpj_syevj_mp", "mpj_syevj_plain", "mpj_syevj_workspace_bytes",
            "mpj_stage1_syevj32", "mpj_mgs", "mpj_mgs_workspace_bytes", "mpj_mgs_noalloc",
            "mpj_congruence", "mpj_congruence_workspace_bytes",
            "mpj_sweeps", "mpj_sweeps_workspace_bytes",
-           "mpj_profile_enable", "mpj_profile_reset", "mpj_profile_read", "mpj_profile_name",
+           "mpj_profile_enable", "mpj_profile_reset", "mpj_profile_read", "mpj_profile_units", "mpj_profile_name",
            "mpj_profile_classes", "mpj_kernel_launches",
            "mpj_batch_plan_create", "mpj_batch_plan_info", "mpj_syevj_batched",
            "mpj_batch_plan_destroy", "mpj_syev_backward_batched",
@@ -135,6 +135,7 @@ def lib():
         L.mpj_profile_reset.argtypes = []; L.mpj_profile_reset.restype = None
         L.mpj_profile_read.argtypes = [i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(d)]
         L.mpj_profile_read.restype = i
+        L.mpj_profile_units.argtypes = [i, ctypes.POINTER(d)]; L.mpj_profile_units.restype = i
         L.mpj_profile_name.argtypes = [i]; L.mpj_profile_name.restype = ctypes.c_char_p
         L.mpj_profile_classes.argtypes = []; L.mpj_profile_classes.restype = i
         L.mpj_kernel_launches.argtypes = []; L.mpj_kernel_launches.restype = ctypes.c_ulonglong
@@ -342,6 +343,17 @@ def profile_read():
         n, ms = ctypes.c_longlong(), ctypes.c_double()
         L.mpj_profile_read(k, ctypes.byref(n), ctypes.byref(ms))
         out[L.mpj_profile_name(k).decode()] = (n.value, ms.value)
+    return out
+
+
+def profile_units():
+    """{kernel class: algorithmic bytes counted by the library} since the last reset."""
+    L = lib()
+    out = {}
+    for k in range(L.mpj_profile_classes()):
+        v = ctypes.c_double()
+        L.mpj_profile_units(k, ctypes.byref(v))
+        out[L.mpj_profile_name(k).decode()] = v.value
     return out
 
 

@@ -183,10 +183,9 @@ int stage1_evd(const double* A, int lda, int n, int N, int B, double normA, cons
     MPJ_TRY(set_identity_f32(b.V32, N, N, N, s));
     const bool tc = B == 32 && !knobs().simt_stage1;
     if (tc) {
-        // tensor-core engine: V32 holds V row-major; the FP64 T buffer (unused until
-        // step 3) is the scratch P of its two passes
-        MPJ_TRY(twosided_sweeps_tc32(b.T32, b.V32, reinterpret_cast<float*>(b.T64), N, n,
-                                     op.tol1 * normA, kUps, op.max_sweeps1, op.max_inner, b.eng, s, r1));
+        // tensor-core engine: V32 holds V row-major
+        MPJ_TRY(twosided_sweeps_tc32(b.T32, b.V32, N, n, op.tol1 * normA, kUps, op.max_sweeps1, op.max_inner,
+                                     b.eng, s, r1));
     } else {
         MPJ_TRY(twosided_sweeps<float>(b.T32, b.V32, N, n, B, op.tol1 * normA, kUps, op.max_sweeps1,
                                        op.max_inner, b.eng, s, r1));

@@ -115,7 +115,7 @@ enum ProfClass {
     PC_MGS_PROJ, PC_GRAM1_F32, PC_SOLVE1_F32, PC_APPLY1_F32, PC_GRAM1_F64, PC_SOLVE1_F64,
     PC_APPLY1_F64, PC_AUX, PC_APPLY2V_F32, PC_APPLY2V_F64, PC_BATCHED, PC_TC1_F32, PC_TC2_F32,
     PC_OZ_SLICE, PC_OZ_GEMM, PC_TCV_F32, PC_TCP1_F64, PC_TCP2_F64, PC_TCV_F64, PC_GRAM_TC64,
-    PC_TCC_F64, PC_TCV1_F64, kProfClasses
+    PC_TCC_F64, PC_TCV1_F64, PC_TILE_F32, kProfClasses
 };
 struct ProfScope {
     int cls;
@@ -125,6 +125,8 @@ struct ProfScope {
     ~ProfScope();
 };
 void prof_flush();
+// Add algorithmic bytes to a class's work count (mpj_profile_units).
+void prof_add_units(int cls, double bytes);
 // Per-sweep trace on stderr (rotation counts, off-norms): MPJ_OPT_TRACE.
 inline bool trace_on() { return knobs().trace; }
 #define MPJ_PROF(cls, stream) ::mpj::ProfScope _mpj_prof_scope((cls), (stream))
@@ -151,12 +153,11 @@ int twosided_sweeps(Real* T, Real* V, int N, int n, int B, double tol_abs, doubl
                     int max_sweeps, int max_inner, void* work, cudaStream_t s, SweepResult* res);
 
 // The FP32 engine of step 1 with the rotations applied on the tensor cores
-// (tc_apply.cu): block size b = 32 (N a multiple of 64), T and P column-major
-// N x N (P: scratch of N^2 floats), Vt = V^T column-major (V row-major).
+// (tc_apply.cu): block size b = 32 (N a multiple of 64), T column-major N x N
+// and symmetric, Vt = V^T column-major (V row-major).
 size_t tc32_workspace_bytes(int N);
-int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol_abs,
-                         double eps_skip, int max_sweeps, int max_inner, void* work, cudaStream_t s,
-                         SweepResult* res);
+int twosided_sweeps_tc32(float* T, float* Vt, int N, int n, double tol_abs, double eps_skip, int max_sweeps,
+                         int max_inner, void* work, cudaStream_t s, SweepResult* res);
 // The FP64 engine with the rotations applied on the tensor cores by exact
 // splitting (tc64_apply.cu): block size b = 32, T and V column-major N x N.
 // The workspace holds the block rotations, their digit planes and the N x N

@@ -16,6 +16,7 @@ bool g_on = false;
 unsigned long long g_total = 0;
 long long g_count[kProfClasses] = {};
 double g_ms[kProfClasses] = {};
+double g_units[kProfClasses] = {};
 std::vector<Pending> g_pending;
 std::vector<cudaEvent_t> g_pool;
 
@@ -29,7 +30,7 @@ const char* kNames[kProfClasses] = {
     "solve2_f32", "apply2_f32", "solve2_f64", "apply2_f64", "dgemm_f64", "mgs_panel",
     "mgs_proj", "gram1_f32", "solve1_f32", "apply1_f32", "gram1_f64", "solve1_f64",
     "apply1_f64", "aux", "apply2v_f32", "apply2v_f64", "batched", "tc1_f32", "tc2_f32", "oz_slice", "oz_gemm", "tcv_f32",
-    "tcp1_f64", "tcp2_f64", "tcv_f64", "gram_tc64", "tcc_f64", "tcv1_f64"};
+    "tcp1_f64", "tcp2_f64", "tcv_f64", "gram_tc64", "tcc_f64", "tcv1_f64", "tile_f32"};
 }  // namespace
 
 ProfScope::ProfScope(int cls_, cudaStream_t s_) : cls(cls_), s(s_) {
@@ -49,6 +50,11 @@ ProfScope::~ProfScope() {
     if (!b) return;
     cudaEventRecord(b, s);
     g_pending.push_back({cls, a, b});
+}
+
+void prof_add_units(int cls, double bytes) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_units[cls] += bytes;
 }
 
 // Accumulate the elapsed times of launches whose end events have completed.
@@ -78,7 +84,7 @@ void mpj_profile_enable(int on) {
 void mpj_profile_reset(void) {
     mpj::prof_flush();
     std::lock_guard<std::mutex> lk(mpj::g_mu);
-    for (int i = 0; i < mpj::kProfClasses; ++i) { mpj::g_count[i] = 0; mpj::g_ms[i] = 0.0; }
+    for (int i = 0; i < mpj::kProfClasses; ++i) { mpj::g_count[i] = 0; mpj::g_ms[i] = 0.0; mpj::g_units[i] = 0.0; }
 }
 
 int mpj_profile_read(int kclass, long long* launches, double* total_ms) {
@@ -87,6 +93,13 @@ int mpj_profile_read(int kclass, long long* launches, double* total_ms) {
     std::lock_guard<std::mutex> lk(mpj::g_mu);
     if (launches) *launches = mpj::g_count[kclass];
     if (total_ms) *total_ms = mpj::g_ms[kclass];
+    return MPJ_SUCCESS;
+}
+
+int mpj_profile_units(int kclass, double* bytes) {
+    if (kclass < 0 || kclass >= mpj::kProfClasses || !bytes) return MPJ_BAD_ARG;
+    std::lock_guard<std::mutex> lk(mpj::g_mu);
+    *bytes = mpj::g_units[kclass];
     return MPJ_SUCCESS;
 }
 

@@ -106,13 +106,7 @@ __device__ __forceinline__ void tmem_ld2(uint32_t taddr, float& v0, float& v1) {
     v1 = __uint_as_float(r1);
 }
 
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            tc::smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(tc::smem_u32(mbar))
-        : "memory");
-}
+using tc::bulk_load;
 
 // Byte offset of X(m, c) in the FP64 tile.  Column layout (Lc): two TMA boxes
 // of 128 rows x 32 columns, column c at c * 1024.  Row layout (Lr): four boxes
@@ -152,9 +146,7 @@ __device__ __forceinline__ void tile_io(const CUtensorMap* map, bool load, unsig
     }
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
-}
+using tc::mbar_arrive;
 
 // Named barrier over `count` threads that also ORs a predicate across them, so
 // that every thread of a role takes the same decision.

@@ -3,27 +3,23 @@
 //
 // A round of the parallel order replaces T by W^T T W and V by V W, where W is
 // block diagonal over the disjoint block pairs (I, J) of the round (one 2b x 2b
-// orthogonal block W_b = I + F_b per pair, from the block-pair solves).  Both
-// are written as right multiplications of 128-row slabs by W_b:
+// orthogonal block W_b = I + F_b per pair, from the block-pair solves):
 //
-//   pass 1   P = T W          P[rows, IJ_b] = T[rows, IJ_b] + T[rows, IJ_b] F_b
-//   pass 2   T' = P^T W       (= W^T T W, as T is symmetric), and V' = V W
+//   tile pass   T'[IJ_a, IJ_b] = W_a^T T[IJ_a, IJ_b] W_b for every a < b, written
+//               with its mirror (the diagonal blocks are the solver's)
+//   slab pass   V'[rows, IJ_b] = V[rows, IJ_b] W_b for 128-row slabs of V
 //
-// Every tile is one 128 x 64 x 64 product on the tensor cores in delta form
-// (X + X F), with X and F split into TF32 pairs (hi + lo) and the three
-// products hi*hi + hi*lo + lo*hi accumulated in FP32 in TMEM, which carries
-// about 21 bits of each product -- the accuracy of the FP32 SIMT products it
-// replaces.  The operand X must be K-major (the 64 columns of the pair
-// contiguous for each row): T is read through its transpose (T and P are
-// column-major, so T^T[rows, IJ_b] is contiguous along IJ_b), and V is kept
-// row-major (Vt = V^T column-major).  Pass 1 and pass 2 write column-major
-// (each warp stores 32 consecutive rows of one column); V is written row-major
-// through a shared-memory staging tile.
+// Every product runs on the tensor cores in delta form (X + X F), with X and F
+// split into TF32 pairs (hi + lo) and the three products hi*hi + hi*lo + lo*hi
+// accumulated in FP32 in TMEM, which carries about 21 bits of each product --
+// the accuracy of the FP32 SIMT products it replaces.  Operands are K-major:
+// T tiles are read through the transposed view that T's symmetry allows, V is
+// kept row-major (Vt = V^T column-major), and the rotations are stored as TF32
+// images of F_b^T.
 //
-// Traffic per round: T and P are read and written once each, V read and written
-// once: 6 N^2 floats.  The block-pair solves are the FP32 k_solve2 kernels of
-// the SIMT engine, without writing the rotated block back (pass 1 and 2 rotate
-// the diagonal blocks too).
+// Traffic per round: the off-diagonal tiles of T read once and written twice
+// (3 N (N - 2b) floats), V read and written once (2 N^2 floats).  The block-pair
+// solves are the FP32 pair solves of the SIMT engine.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -49,216 +45,537 @@ constexpr int kM = 2 * kB;
 constexpr int kSolve32Threads = 1024;
 
 
-__global__ void __launch_bounds__(kSolve32Threads)
-k_solve2_nb(float* __restrict__ T, int N, float* __restrict__ Fbuf, float* __restrict__ Sbuf,
-            float* __restrict__ Fimg, float* __restrict__ fmax, int round, float eps, float tau,
-            float gate, int max_inner, int cross, unsigned long long* __restrict__ rot_counter) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    int applied = pair_solve<float, kB, false>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
-                                               Fbuf + (size_t)blockIdx.x * kM * kM,
-                                               fmax + blockIdx.x, smraw,
-                                               Sbuf + (size_t)blockIdx.x * kM * kM, cross ? round : -1);
-    if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
-    // TF32 hi / lo image of F_b^T (row n, column k holds F_b[k][n]) for the pass
-    // kernel's B operand; the block's F is still in shared memory (after S).
-    const float* Fs = reinterpret_cast<const float*>(smraw) + kM * (kM + 1);
-    float* img = Fimg + (size_t)blockIdx.x * 2 * kM * kM;
+// The TF32 image of a block rotation F_b, the B operand of the slab pass and of
+// product 1 of the tile pass and the A operand of product 2: row n holds
+// F_b[:, n] (K-major), split into hi and lo planes, each plane two chunks of 64
+// rows x 32 floats (k < 32, k >= 32) in the 128-byte swizzled order that a
+// 1024-byte aligned shared-memory copy of it needs.  One pair's image is 32 KB,
+// contiguous, so that one bulk copy loads it.
+constexpr int kFChunk = kM * 32;                     // floats of one image chunk (8 KB)
+constexpr int kFImage = 4 * kFChunk;                 // floats of one pair's image
+constexpr uint32_t kFImageBytes = sizeof(float) * kFImage;
+
+__device__ __forceinline__ int fimg_off(int n, int k) {
+    return (k >> 5) * kFChunk + tc::sw128_off(n, (k & 31) >> 2) + (k & 3);
+}
+
+// Image of one F (element F[k][n] = at(k, n)) into img, by the whole block.
+template <class At>
+__device__ __forceinline__ void write_fimage(float* __restrict__ img, At at) {
     for (int t = threadIdx.x; t < kM * kM; t += blockDim.x) {
         const int n = t / kM, k = t % kM;
         float h, l;
-        tc::split_tf32(Fs[n * (kM + 1) + k], h, l);
-        img[t] = h;
-        img[kM * kM + t] = l;
+        tc::split_tf32(at(k, n), h, l);
+        img[fimg_off(n, k)] = h;
+        img[2 * kFChunk + fimg_off(n, k)] = l;
     }
 }
 
-// Per-CTA shared memory of the pass kernel (offsets in floats from a 1024-byte
-// aligned base): the load slot -- the two 32-column chunks of the X tile (128
-// rows x 128 bytes, 128-byte swizzle, as the TMA writes them; split in place
-// into the TF32 hi part) and the TF32 hi/lo image of F_b^T for the two K halves
-// (64 rows x 128 bytes each) -- then the TF32 lo part of X.  96 KB: two CTAs
-// share an SM, so one's loads overlap the other's MMAs and stores.
-constexpr int kChunk = kSlab * 32;                   // floats of one X chunk (16 KB)
-constexpr int kFChunk = kM * 32;                     // floats of one F chunk (8 KB)
-constexpr int kSlotFloats = 2 * kChunk + 4 * kFChunk;
-constexpr int kXlOff = kSlotFloats;
-constexpr size_t kPassSmem = sizeof(float) * (size_t)(kXlOff + 2 * kChunk) + 1024;
-constexpr uint32_t kSlotBytes = sizeof(float) * kSlotFloats;   // TMA bytes per item
+// Block-pair solves of one round.  The rotated block goes back to T: the tile
+// pass updates the off-diagonal tiles only.
+__global__ void __launch_bounds__(kSolve32Threads)
+k_solve2_nb(float* __restrict__ T, int N, float* __restrict__ Fbuf, float* __restrict__ Fimg,
+            float* __restrict__ fmax, int round, float eps, float tau, float gate, int max_inner, int cross,
+            unsigned long long* __restrict__ rot_counter) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    int applied = pair_solve<float, kB, true>(T, N, round, blockIdx.x, eps, tau, gate, max_inner,
+                                              Fbuf + (size_t)blockIdx.x * kM * kM, fmax + blockIdx.x, smraw,
+                                              nullptr, cross ? round : -1);
+    if (threadIdx.x == 0 && applied) atomicAdd(rot_counter, (unsigned long long)applied);
+    // the block's F is still in shared memory (after S), column-major with ld 2b + 1
+    const float* Fs = reinterpret_cast<const float*>(smraw) + kM * (kM + 1);
+    write_fimage(Fimg + (size_t)blockIdx.x * kFImage, [&](int k, int n) { return Fs[n * (kM + 1) + k]; });
+}
+
+// ---------------------------------------------------------------- slab pass
+// X <- X + X F_b for the 128-row slabs of a row-major X (V, or C of the SVD)
+// and every pair b: X[rows, IJ_b] is two TMA boxes of 128 rows x 32 floats
+// (K-major), F_b's image one bulk copy.  One 128 x 64 x 64 product per item in
+// delta form with the three-term TF32 split, stored back in place by TMA.
+// Items whose W_b is the identity are skipped.
+//
+// Shared memory: three regions of 32 KB from a 1024-byte aligned base.  Q holds
+// the TF32 lo part of the slab and then the staging of the result; the other
+// two take turns as the slab (split in place to hi) and the F image: once item
+// k's product has completed, its F region receives slab k + 1, and once the
+// slab has been drained, its region receives F for item k + 1.  The three terms
+// are issued by three warps into three 64-column accumulators (one thread
+// issues tcgen05.mma at about 80 cycles an instruction); lane 0 of warp 3
+// issues the copies.  Two CTAs share an SM.
+constexpr int kChunk = kSlab * 32;                   // floats of one slab chunk (16 KB)
+constexpr int kRegion = 2 * kChunk;                  // floats of one region (32 KB)
+constexpr size_t kPassSmem = sizeof(float) * (size_t)(3 * kRegion) + 1024;
+constexpr uint32_t kXBytes = sizeof(float) * kRegion;
+constexpr int kPassTmemCols = 256;                   // three 64-column accumulators
 
 struct PassMaps {
-    CUtensorMap in_t;       // X source of the T tiles (T in pass 1, P in pass 2)
-    CUtensorMap v;          // Vt (row-major V), loads and stores
-    CUtensorMap f;          // F image: (pairs x 128) rows of 64 floats
+    CUtensorMap x;          // row-major X (rows of N floats), boxes of 128 rows x 32 floats
 };
 
-// The item sequence of a CTA: it, it + gridDim.x, ...; V tiles whose W_b is the
-// identity are skipped (they are unchanged).
-__device__ __forceinline__ int next_item(int it, int total, int items_T, int n_slabs,
-                                         const float* __restrict__ fmax) {
-    while (it < total && it >= items_T && fmax[(it - items_T) / n_slabs] == 0.f) it += gridDim.x;
+__device__ __forceinline__ int next_item(int it, int total, int n_slabs, const float* __restrict__ fmax) {
+    while (it < total && fmax[it / n_slabs] == 0.f) it += gridDim.x;
     return it;
 }
 
-__device__ __forceinline__ void issue_item(const PassMaps& maps, int it, int items_T, int n_slabs,
-                                           int round, int nblocks, float* slot, uint64_t* full) {
-    const bool vt = it >= items_T;
-    const int item = vt ? it - items_T : it;
-    const int s = item % n_slabs, b = item / n_slabs;
+__device__ __forceinline__ void issue_slab(const PassMaps& maps, int it, int n_slabs, int round, int nblocks,
+                                           float* dst, uint64_t* bar) {
+    const int s = it % n_slabs, b = it / n_slabs;
     int I, J;
     round_pair(round, b, nblocks, I, J);
-    const CUtensorMap* mx = vt ? &maps.v : &maps.in_t;
-    tc::mbar_expect_tx(full, kSlotBytes);
-    tc::tma_load_2d(slot, mx, I * kB, s * kSlab, full);
-    tc::tma_load_2d(slot + kChunk, mx, J * kB, s * kSlab, full);
-    float* F = slot + 2 * kChunk;
-    tc::tma_load_2d(F, &maps.f, 0, b * 2 * kM, full);                      // hi, k < 32
-    tc::tma_load_2d(F + kFChunk, &maps.f, 32, b * 2 * kM, full);           // hi, k >= 32
-    tc::tma_load_2d(F + 2 * kFChunk, &maps.f, 0, b * 2 * kM + kM, full);   // lo, k < 32
-    tc::tma_load_2d(F + 3 * kFChunk, &maps.f, 32, b * 2 * kM + kM, full);  // lo, k >= 32
+    tc::mbar_expect_tx(bar, kXBytes);
+    tc::tma_load_2d(dst, &maps.x, I * kB, s * kSlab, bar);
+    tc::tma_load_2d(dst + kChunk, &maps.x, J * kB, s * kSlab, bar);
 }
 
-// Persistent pass kernel (two CTAs per SM).  Items [0, items_T): Tout[rows, IJ_b]
-// = X + X F_b with X[m][k] = In[col(k) + (row0 + m) N] (In^T, K-major), written
-// column-major; with Sbuf the rows in IJ_b take the solver's rotated block
-// instead.  Items [items_T, total): the rows slab of the row-major V times W_b,
-// stored back with TMA.
 __global__ void __launch_bounds__(kTcThreads, 2)
-k_pass_tc(const __grid_constant__ PassMaps maps, float* __restrict__ Tout, int N, int n_slabs,
-          int items_T, int total, const float* __restrict__ Sbuf, const float* __restrict__ fmax,
-          int round, int terms, unsigned long long* __restrict__ err) {
+k_pass_tc(const __grid_constant__ PassMaps maps, const float* __restrict__ Fimg, int N, int n_slabs, int total,
+          const float* __restrict__ fmax, int round, int terms, unsigned long long* __restrict__ err) {
     extern __shared__ unsigned char smraw[];
-    float* sl = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full;
-    __shared__ __align__(8) uint64_t mma_done;
+    float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    float* Q = base + 2 * kRegion;
+    __shared__ __align__(8) uint64_t fullX, fullF, qfree, mma_done;
     __shared__ uint32_t tmem_slot;
-    float* Xh = sl;                                  // split in place
-    float* Xl = sl + kXlOff;
-    const float* F = sl + 2 * kChunk;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nblocks = N / kB;
+    const int nterm = terms == 3 ? 3 : 1;
+    const bool mma_lane = lane == 0 && warp < nterm;
+    const bool copy_lane = tid == 96;
     if (tid == 0) {
-        tc::mbar_init(&full, 1);
-        tc::mbar_init(&mma_done, 1);
+        tc::mbar_init(&fullX, 1);
+        tc::mbar_init(&fullF, 1);
+        tc::mbar_init(&qfree, 1);
+        tc::mbar_init(&mma_done, nterm);
         tc::fence_mbar_init();
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, kM);
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kPassTmemCols);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_slot;
-    const int it0 = next_item(blockIdx.x, total, items_T, n_slabs, fmax);
-    if (tid == 0 && it0 < total) issue_item(maps, it0, items_T, n_slabs, round, nblocks, sl, &full);
+    const int m = warp * 32 + lane;                      // slab row = accumulator row
+    const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+    const int it0 = next_item(blockIdx.x, total, n_slabs, fmax);
+    if (copy_lane) {
+        tc::mbar_arrive(&qfree);                         // Q starts free (phase 0)
+        if (it0 < total) {
+            issue_slab(maps, it0, n_slabs, round, nblocks, base, &fullX);
+            tc::mbar_expect_tx(&fullF, kFImageBytes);
+            tc::bulk_load(base + kRegion, Fimg + (size_t)(it0 / n_slabs) * kFImage, kFImageBytes, &fullF);
+        }
+    }
     bool ok = true;
+    constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, kSlab, kM);
     int k = 0;
     for (int it = it0; it < total; ++k) {
-        const bool vt = it >= items_T;
-        const int item = vt ? it - items_T : it;
-        const int s = item % n_slabs, b = item / n_slabs;
+        float* X = base + (k & 1) * kRegion;            // the slab's region
+        float* F = base + ((k + 1) & 1) * kRegion;      // the F image's region
+        const int s = it % n_slabs, b = it / n_slabs;
         int I, J;
         round_pair(round, b, nblocks, I, J);
         const int row0 = s * kSlab;
-        ok = tc::mbar_wait(&full, k & 1, kTcWait) && ok;         // waited even after an error
-        // split X in place: hi over the loaded tile, lo to Xl (same swizzled offsets)
+        const int itn = next_item(it + gridDim.x, total, n_slabs, fmax);
+        ok = tc::mbar_wait(&fullX, k & 1, kTcWait) && ok;          // waited even after an error
+        ok = tc::mbar_wait(&qfree, k & 1, kTcWait) && ok;
+        // split the slab in place: hi over it, lo to Q (same swizzled offsets)
 #pragma unroll 4
-        for (int i = tid; i < 2 * kChunk / 4; i += kTcThreads) {
-            const float4 x = reinterpret_cast<const float4*>(Xh)[i];
+        for (int i = tid; i < kRegion / 4; i += kTcThreads) {
+            const float4 x = reinterpret_cast<const float4*>(X)[i];
             float4 h, l;
             tc::split_tf32(x.x, h.x, l.x);
             tc::split_tf32(x.y, h.y, l.y);
             tc::split_tf32(x.z, h.z, l.z);
             tc::split_tf32(x.w, h.w, l.w);
-            reinterpret_cast<float4*>(Xh)[i] = h;
-            reinterpret_cast<float4*>(Xl)[i] = l;
+            reinterpret_cast<float4*>(X)[i] = h;
+            reinterpret_cast<float4*>(Q)[i] = l;
         }
+        ok = tc::mbar_wait(&fullF, k & 1, kTcWait) && ok;
         tc::fence_proxy_async();
         tc::fence_before_sync();
         __syncthreads();
         tc::fence_after_sync();
-        if (tid == 0 && ok) {
-            constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, kSlab, kM);
+        if (mma_lane && ok) {            // term of this warp: 0 hi hi, 1 lo hi, 2 hi lo
+            const float* A = warp == 1 ? Q : X;
+            const float* B = F + (warp == 2 ? 2 * kFChunk : 0);
+            const uint32_t d = tmem + (uint32_t)(64 * warp);
 #pragma unroll
-            for (int ks = 0; ks < kM / 8; ++ks) {          // K = 8 per MMA, 32 bytes along the row
+            for (int ks = 0; ks < kM / 8; ++ks) {      // K = 8 per MMA, 32 bytes along the row
                 const int ch = ks >> 2;
                 const uint32_t off = (ks & 3) * 32;
-                const uint32_t xh = tc::smem_u32(Xh + ch * kChunk) + off;
-                const uint32_t xl = tc::smem_u32(Xl + ch * kChunk) + off;
-                const uint32_t fh = tc::smem_u32(F + ch * kFChunk) + off;
-                const uint32_t fl = tc::smem_u32(F + (2 + ch) * kFChunk) + off;
-                if (terms == 3) {            // the two cross terms of the three-term split
-                    tc::mma_tf32(tmem, tc::smem_desc_sw128(xl), tc::smem_desc_sw128(fh), idesc, ks > 0);
-                    tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fl), idesc, 1);
-                }
-                tc::mma_tf32(tmem, tc::smem_desc_sw128(xh), tc::smem_desc_sw128(fh), idesc,
-                             terms == 3 || ks > 0);
+                tc::mma_tf32(d, tc::smem_desc_sw128(tc::smem_u32(A + ch * kChunk) + off),
+                             tc::smem_desc_sw128(tc::smem_u32(B + ch * kFChunk) + off), idesc, ks > 0);
             }
             tc::commit(&mma_done);
         }
         ok = tc::mbar_wait(&mma_done, k & 1, kTcWait) && ok;
         tc::fence_after_sync();
-        const int m = warp * 32 + lane;
-        const int row = row0 + m;
+        if (copy_lane && itn < total) issue_slab(maps, itn, n_slabs, round, nblocks, F, &fullX);   // F is dead
         float o[kM];
-        if (ok) {
 #pragma unroll
-            for (int c0 = 0; c0 < kM; c0 += 16)
-                tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, o + c0);
-            tc::tmem_wait_ld();
+        for (int c0 = 0; c0 < kM; c0 += 16) {
+            float w[16];
+            tc::tmem_ld16(lanebase + (uint32_t)c0, o + c0);
+            if (nterm == 3) {
+                tc::tmem_ld16(lanebase + 64 + (uint32_t)c0, w);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) o[c0 + j] += w[j];
+                tc::tmem_ld16(lanebase + 128 + (uint32_t)c0, w);
+                tc::tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 16; ++j) o[c0 + j] += w[j];
+            }
+        }
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {                   // delta form: + X (= hi + lo exactly)
+                const int off = ch * kChunk + tc::sw128_off(m, j);
+                const float4 h = *reinterpret_cast<const float4*>(X + off);
+                const float4 l = *reinterpret_cast<const float4*>(Q + off);
+                float* oo = o + ch * 32 + j * 4;
+                oo[0] += h.x + l.x; oo[1] += h.y + l.y; oo[2] += h.z + l.z; oo[3] += h.w + l.w;
+            }
+        tc::fence_before_sync();
+        __syncthreads();                                 // the slab, Q and TMEM are read
+        if (copy_lane && itn < total) {                  // the slab region takes the next F
+            tc::mbar_expect_tx(&fullF, kFImageBytes);
+            tc::bulk_load(X, Fimg + (size_t)(itn / n_slabs) * kFImage, kFImageBytes, &fullF);
+        }
+        if (ok) {                                        // staging in Q, the slab's layout
 #pragma unroll
             for (int ch = 0; ch < 2; ++ch)
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {               // delta form: + X (= hi + lo exactly)
-                    const int off = ch * kChunk + tc::sw128_off(m, j);
-                    const float4 h = *reinterpret_cast<const float4*>(Xh + off);
-                    const float4 l = *reinterpret_cast<const float4*>(Xl + off);
-                    float* oo = o + ch * 32 + j * 4;
-                    oo[0] += h.x + l.x; oo[1] += h.y + l.y; oo[2] += h.z + l.z; oo[3] += h.w + l.w;
+                for (int j = 0; j < 8; ++j) {
+                    const float* oo = o + ch * 32 + j * 4;
+                    *reinterpret_cast<float4*>(Q + ch * kChunk + tc::sw128_off(m, j)) =
+                        make_float4(oo[0], oo[1], oo[2], oo[3]);
                 }
+            tc::fence_proxy_async();
         }
-        if (!vt) {
-            if (ok && row < N) {
-                if (Sbuf && (row / kB == I || row / kB == J)) {
-                    const float* Sr = Sbuf + (size_t)b * kM * kM +
-                                      (size_t)(row / kB == I ? row % kB : kB + row % kB) * kM;
-#pragma unroll
-                    for (int c = 0; c < kM; ++c) o[c] = __ldg(Sr + c);
-                }
-#pragma unroll
-                for (int c = 0; c < kM; ++c) Tout[(size_t)row + (size_t)pair_global(c, I, J, kB) * N] = o[c];
-            }
-        } else {
-            __syncthreads();                         // every thread has read its X row
+        __syncthreads();                                 // the staging is written
+        if (copy_lane) {
             if (ok) {
-                // stage over the X tile and store with TMA
-#pragma unroll
-                for (int ch = 0; ch < 2; ++ch)
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float* oo = o + ch * 32 + j * 4;
-                        *reinterpret_cast<float4*>(Xh + ch * kChunk + tc::sw128_off(m, j)) =
-                            make_float4(oo[0], oo[1], oo[2], oo[3]);
-                    }
-                tc::fence_proxy_async();
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();                             // TMEM, X and the staging tile are settled
-        const int itn = next_item(it + gridDim.x, total, items_T, n_slabs, fmax);
-        if (tid == 0) {
-            if (vt && ok) {
-                tc::tma_store_2d(&maps.v, I * kB, row0, Xh);
-                tc::tma_store_2d(&maps.v, J * kB, row0, Xh + kChunk);
+                tc::tma_store_2d(&maps.x, I * kB, row0, Q);
+                tc::tma_store_2d(&maps.x, J * kB, row0, Q + kChunk);
                 tc::bulk_commit();
-                tc::bulk_wait_read();                // the slot is reloaded next
+                tc::bulk_wait_read();
             }
-            if (itn < total) issue_item(maps, itn, items_T, n_slabs, round, nblocks, sl, &full);
+            tc::mbar_arrive(&qfree);                     // Q may take the next lo part
         }
         it = itn;
     }
-    if (!ok && tid == 0) atomicExch(err, 1ull);
-    if (tid == 0) tc::bulk_wait_all();
+    if (copy_lane) tc::bulk_wait_all();
+    if (!ok) atomicExch(err, 1ull);
     tc::fence_before_sync();
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tmem, kM);
+    if (warp == 0) tc::tmem_dealloc(tmem, kPassTmemCols);
+}
+
+// ---------------------------------------------------------------- one-pass tile update
+// T' = W^T T W in one pass over the off-diagonal pair tiles: for a < b,
+//
+//   X = T_ab + T_ab F_b            (product 1: M = 64 rows m of IJ_a, N = K = 64)
+//   Y = X + F_a^T X                (product 2: M = 64 rows j of IJ_a, K over m)
+//
+// and Y is stored at T[IJ_a, IJ_b] and, transposed, at T[IJ_b, IJ_a] (T' is
+// symmetric by construction).  T is read once through the K-major view of the
+// T[IJ_b, IJ_a] sub-blocks (T symmetric) and written in place: the two regions
+// of tile (a, b) belong to no other tile.  The diagonal blocks are the block
+// solver's (written back by it).  Both products are three-term TF32 with FP32
+// accumulation in TMEM, as in the slab pass.
+//
+// Shared memory, 8 KB chunks of 64 rows x 128 bytes (128-byte swizzle):
+//   R0  chunks 0-1   T tile (K-major, chunk = k half), split in place to TF32 hi
+//   R1  chunks 2-3   TF32 lo of the T tile
+//   R2  chunks 4-7   F_b image; after product 1 X^T hi / lo (rows n, chunk = m
+//                    half), the B operand of product 2
+//   R3  chunks 8-11  F_a image, the A operand of product 2 (row j holds F_a[:, j]);
+//                    after product 2 the staging of Y (rows m, chunk = n half)
+//   then max |F| of every pair (K floats).
+// A thread holds half a row of Y: T[IJ_a, IJ_b] = Y is written from registers
+// (a warp's 16 rows are 64-byte column segments), T[IJ_b, IJ_a] = Y^T through the
+// staging and TMA.
+// A single thread issues tcgen05.mma at about one instruction per 80 cycles,
+// slower than the tensor core runs these 64 x 64 x 8 products, so the three
+// terms of a product are issued by three warps (lane 0 of warps 0, 1, 2) into
+// three accumulators of 64 TMEM columns, which the drains add.  Lane 0 of warp 3
+// issues the copies while the products run: the store of the previous tile's
+// staging and this tile's F_a during product 1, the next T tile (R0, R1 dead)
+// during product 2, the next F_b once product 2 has completed.
+// The M = 64 accumulator holds row i in TMEM lane 32 (i / 16) + i % 16; each warp
+// drains its 16 rows, lanes 16-31 taking the upper 32 columns through a shuffle.
+constexpr int kTileChunks = 12;
+constexpr uint32_t kTileTBytes = sizeof(float) * 2 * kFChunk;       // the T tile
+size_t tile_smem_bytes(int K) { return sizeof(float) * ((size_t)kTileChunks * kFChunk + (size_t)K) + 1024; }
+
+struct TileMaps {
+    CUtensorMap t;          // T, boxes of 32 x 32
+};
+
+__device__ __forceinline__ int next_tile(int t, int ntiles, int K, const float* fm, int& a, int& b) {
+    for (; t < ntiles; t += gridDim.x) {
+        decode_tile(t, K, a, b);
+        if (fm[a] != 0.f || fm[b] != 0.f) break;         // W_a = W_b = I: unchanged
+    }
+    return t;
+}
+
+__device__ __forceinline__ void issue_tile_t(const TileMaps& maps, int Ia, int Ja, int Ib, int Jb, float* R0,
+                                             uint64_t* bar) {
+    tc::mbar_expect_tx(bar, kTileTBytes);
+#pragma unroll
+    for (int c = 0; c < 2; ++c)                          // k half: columns I_b, J_b of the tile
+#pragma unroll
+        for (int r = 0; r < 2; ++r)                      // m half: rows I_a, J_a of the tile
+            tc::tma_load_2d(R0 + c * kFChunk + r * 32 * 32, &maps.t, (c ? Jb : Ib) * kB, (r ? Ja : Ia) * kB, bar);
+}
+
+__device__ __forceinline__ void issue_fimage(const float* __restrict__ Fimg, int p, float* dst, uint64_t* bar) {
+    tc::mbar_expect_tx(bar, kFImageBytes);
+    tc::bulk_load(dst, Fimg + (size_t)p * kFImage, kFImageBytes, bar);
+}
+
+constexpr int kTileTmemCols = 256;                   // three 64-column accumulators
+
+// 32 columns [32 h, 32 h + 32) of row 16 (warp) + lane % 16 of the sum of the
+// nacc accumulators (64 columns apart) for h = lane / 16: lanes 16-31 receive
+// the upper half of lane - 16's row.
+__device__ __forceinline__ void drain_half(uint32_t lanebase, int h, int nacc, float* d) {
+    float v[32], w[32];
+    tc::tmem_ld16(lanebase + 32, v);
+    tc::tmem_ld16(lanebase + 48, v + 16);
+    if (nacc == 3) {
+        tc::tmem_ld16(lanebase + 64 + 32, w);
+        tc::tmem_ld16(lanebase + 64 + 48, w + 16);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += w[j];
+        tc::tmem_ld16(lanebase + 128 + 32, w);
+        tc::tmem_ld16(lanebase + 128 + 48, w + 16);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += w[j];
+    } else {
+        tc::tmem_wait_ld();
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) d[j] = __shfl_up_sync(0xffffffffu, v[j], 16);
+    tc::tmem_ld16(lanebase, v);
+    tc::tmem_ld16(lanebase + 16, v + 16);
+    if (nacc == 3) {
+        tc::tmem_ld16(lanebase + 64, w);
+        tc::tmem_ld16(lanebase + 64 + 16, w + 16);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += w[j];
+        tc::tmem_ld16(lanebase + 128, w);
+        tc::tmem_ld16(lanebase + 128 + 16, w + 16);
+        tc::tmem_wait_ld();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) v[j] += w[j];
+    } else {
+        tc::tmem_wait_ld();
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) d[j] = h ? d[j] : v[j];
+}
+
+// The term of a three-term product issued by this warp (0: hi hi, 1: lo hi,
+// 2: hi lo; A and B each a hi chunk pair followed by a lo chunk pair) into its
+// own accumulator, then a commit to done.
+__device__ __forceinline__ void issue_term(uint32_t tmem, int warp, const float* A, const float* B,
+                                          uint32_t idesc, uint64_t* done) {
+    const float* Ap = A + (warp == 1 ? 2 * kFChunk : 0);
+    const float* Bp = B + (warp == 2 ? 2 * kFChunk : 0);
+    const uint32_t d = tmem + (uint32_t)(64 * warp);
+#pragma unroll
+    for (int ks = 0; ks < kM / 8; ++ks) {
+        const int ch = ks >> 2;
+        const uint32_t off = (ks & 3) * 32;
+        tc::mma_tf32(d, tc::smem_desc_sw128(tc::smem_u32(Ap + ch * kFChunk) + off),
+                     tc::smem_desc_sw128(tc::smem_u32(Bp + ch * kFChunk) + off), idesc, ks > 0);
+    }
+    tc::commit(done);
+}
+
+// Element (row n, column m) of a transposed plane (chunks by m half, rows n):
+// lanes 16-31 visit their rows in the order j ^ 4, which puts their 16-byte
+// units in the other half of the 128-byte row and keeps the stores conflict-free.
+__device__ __forceinline__ int tposed_off(int n, int m) {
+    return (m >> 5) * kFChunk + tc::sw128_off(n, (m & 31) >> 2) + (m & 3);
+}
+
+// T[IJ_b, IJ_a] = Y^T from the staging in R3 (boxes of 32 rows m x 32 floats n).
+__device__ __forceinline__ void store_staging(const TileMaps& maps, const float* R3, int Ia, int Ja, int Ib,
+                                              int Jb) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            tc::tma_store_2d(&maps.t, (c ? Jb : Ib) * kB, (r ? Ja : Ia) * kB, R3 + c * kFChunk + r * 1024);
+    tc::bulk_commit();
+}
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+k_tile_tc(const __grid_constant__ TileMaps maps, float* __restrict__ T, const float* __restrict__ Fimg, int N,
+          int ntiles, const float* __restrict__ fmax, int round, int terms, unsigned long long* __restrict__ err,
+          unsigned long long* __restrict__ tiles_done) {
+    extern __shared__ unsigned char smraw[];
+    float* R0 = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(smraw) + 1023) & ~uintptr_t(1023));
+    float* R1 = R0 + 2 * kFChunk;
+    float* R2 = R0 + 4 * kFChunk;
+    float* R3 = R0 + 8 * kFChunk;
+    float* fm = R0 + kTileChunks * kFChunk;
+    __shared__ __align__(8) uint64_t fullT, fullFb, fullFa, mma_done;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nblocks = N / kB, K = N / kM;
+    const int nterm = terms == 3 ? 3 : 1;                // issuing warps = accumulators
+    if (tid == 0) {
+        tc::mbar_init(&fullT, 1);
+        tc::mbar_init(&fullFb, 1);
+        tc::mbar_init(&fullFa, 1);
+        tc::mbar_init(&mma_done, nterm);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_slot, kTileTmemCols);
+    for (int i = tid; i < K; i += kTcThreads) fm[i] = fmax[i];
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lanebase = tmem + ((uint32_t)(32 * warp) << 16);
+    const int h = lane >> 4;                             // column half of this lane
+    const int m = 16 * warp + (lane & 15);               // tile row (accumulator row)
+    const bool mma_lane = lane == 0 && warp < nterm;    // issues one term of each product
+    const bool copy_lane = tid == 96;                    // issues the asynchronous copies
+    int a, b;
+    int t = next_tile(blockIdx.x, ntiles, K, fm, a, b);
+    if (copy_lane && t < ntiles) {
+        int Ia, Ja, Ib, Jb;
+        round_pair(round, a, nblocks, Ia, Ja);
+        round_pair(round, b, nblocks, Ib, Jb);
+        issue_tile_t(maps, Ia, Ja, Ib, Jb, R0, &fullT);
+        issue_fimage(Fimg, b, R2, &fullFb);
+        issue_fimage(Fimg, a, R3, &fullFa);
+    }
+    bool ok = true;
+    unsigned long long done = 0;
+    int pIa = 0, pJa = 0, pIb = 0, pJb = 0;              // the tile whose staging is pending (copy lane)
+    bool pending = false;
+    constexpr uint32_t idesc = tc::instr_desc(tc::kFmtTF32, kM, kM);
+    for (int k = 0; t < ntiles; ++k) {
+        int Ia, Ja, Ib, Jb;
+        round_pair(round, a, nblocks, Ia, Ja);
+        round_pair(round, b, nblocks, Ib, Jb);
+        int an = 0, bn = 0;
+        const int tn = next_tile(t + gridDim.x, ntiles, K, fm, an, bn);
+        ok = tc::mbar_wait(&fullT, k & 1, kTcWait) && ok;
+        // split the T tile: hi in place, lo to R1 (same swizzled offsets)
+#pragma unroll
+        for (int i = tid; i < 2 * kFChunk / 4; i += kTcThreads) {
+            const float4 x = reinterpret_cast<const float4*>(R0)[i];
+            float4 hh, ll;
+            tc::split_tf32(x.x, hh.x, ll.x);
+            tc::split_tf32(x.y, hh.y, ll.y);
+            tc::split_tf32(x.z, hh.z, ll.z);
+            tc::split_tf32(x.w, hh.w, ll.w);
+            reinterpret_cast<float4*>(R0)[i] = hh;
+            reinterpret_cast<float4*>(R1)[i] = ll;
+        }
+        ok = tc::mbar_wait(&fullFb, k & 1, kTcWait) && ok;
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();                                 // also: the previous staging is written
+        tc::fence_after_sync();
+        if (mma_lane && ok) issue_term(tmem, warp, R0, R2, idesc, &mma_done);   // product 1: D = T_ab F_b
+        if (copy_lane && pending) {                      // the previous tile's Y^T, then this F_a
+            store_staging(maps, R3, pIa, pJa, pIb, pJb);
+            tc::bulk_wait_read();
+            pending = false;
+            issue_fimage(Fimg, a, R3, &fullFa);
+        }
+        ok = tc::mbar_wait(&mma_done, 0, kTcWait) && ok;
+        tc::fence_after_sync();
+        // X = T_ab + D (delta form; hi + lo = T exactly), kept in registers, and
+        // its TF32 split written transposed over F_b
+        float x[32];
+        drain_half(lanebase, h, nterm, x);
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+            const int off = h * kFChunk + tc::sw128_off(m, j4);
+            const float4 th = *reinterpret_cast<const float4*>(R0 + off);
+            const float4 tl = *reinterpret_cast<const float4*>(R1 + off);
+            x[4 * j4 + 0] += th.x + tl.x;
+            x[4 * j4 + 1] += th.y + tl.y;
+            x[4 * j4 + 2] += th.z + tl.z;
+            x[4 * j4 + 3] += th.w + tl.w;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) {
+            const float v = h ? x[jj ^ 4] : x[jj];
+            const int n = 32 * h + (jj ^ (4 * h));
+            float vh, vl;
+            tc::split_tf32(v, vh, vl);
+            R2[tposed_off(n, m)] = vh;
+            R2[2 * kFChunk + tposed_off(n, m)] = vl;
+        }
+        tc::fence_proxy_async();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (mma_lane) {                                  // product 2: D = F_a^T X
+            ok = tc::mbar_wait(&fullFa, k & 1, kTcWait) && ok;
+            if (ok) issue_term(tmem, warp, R3, R2, idesc, &mma_done);
+        }
+        if (copy_lane && tn < ntiles) {                  // R0 and R1 are dead: the next T tile
+            int Ian, Jan, Ibn, Jbn;
+            round_pair(round, an, nblocks, Ian, Jan);
+            round_pair(round, bn, nblocks, Ibn, Jbn);
+            issue_tile_t(maps, Ian, Jan, Ibn, Jbn, R0, &fullT);
+        }
+        ok = tc::mbar_wait(&mma_done, 1, kTcWait) && ok;
+        tc::fence_after_sync();
+        if (copy_lane && tn < ntiles) issue_fimage(Fimg, bn, R2, &fullFb);     // X^T is dead
+        float d[32];
+        drain_half(lanebase, h, nterm, d);
+        tc::fence_before_sync();                         // TMEM is read (product 1 follows a barrier)
+        if (ok) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] += d[j];   // Y row m, columns [32 h, 32 h + 32)
+            // T[IJ_a, IJ_b] = Y: row gm of columns gn0 .. gn0 + 31 (16 lanes: 64 bytes per column)
+            const int gm = m < kB ? Ia * kB + m : Ja * kB + m - kB;
+            const int gn0 = (h ? Jb : Ib) * kB;
+            float* col = T + (size_t)gn0 * N + gm;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) col[(size_t)j * N] = x[j];
+            // staging of Y over F_a (dead since product 2): rows m, chunk = n half
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4)
+                *reinterpret_cast<float4*>(R3 + h * kFChunk + tc::sw128_off(m, j4)) =
+                    make_float4(x[4 * j4], x[4 * j4 + 1], x[4 * j4 + 2], x[4 * j4 + 3]);
+            tc::fence_proxy_async();
+        }
+        if (copy_lane && ok) {
+            ++done;
+            pending = true;
+            pIa = Ia; pJa = Ja; pIb = Ib; pJb = Jb;
+        }
+        t = tn;
+        a = an;
+        b = bn;
+    }
+    __syncthreads();                                     // the last staging is written
+    if (copy_lane) {
+        if (pending) store_staging(maps, R3, pIa, pJa, pIb, pJb);
+        tc::bulk_wait_all();
+        if (done) atomicAdd(tiles_done, done);
+    }
+    if (!ok) atomicExch(err, 1ull);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, kTileTmemCols);
 }
 
 // ---------------------------------------------------------------- one-sided FP32
@@ -401,24 +718,16 @@ k_gram_tc32(const __grid_constant__ CUtensorMap map, int m, int N, int round, in
     if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
-// TF32 hi / lo image of F_b^T (row n, column k: F_b[k][n]) from the block solve's
-// row-major F_b, for the B operand of k_pass_tc, and max |F_b|.
+// TF32 image of F_b (the slab pass's B operand) from the block solve's
+// row-major F_b, and max |F_b|.
 __global__ void __launch_bounds__(256)
 k_fimg32(const float* __restrict__ Wbuf, float* __restrict__ Fimg, float* __restrict__ fmax) {
     __shared__ float red[8];
     const int b = blockIdx.x;
     const float* F = Wbuf + (size_t)b * kM * kM;
-    float* img = Fimg + (size_t)b * 2 * kM * kM;
+    write_fimage(Fimg + (size_t)b * kFImage, [&](int k, int n) { return F[k * kM + n]; });
     float mx = 0.f;
-    for (int t = threadIdx.x; t < kM * kM; t += blockDim.x) {
-        const int n = t / kM, k = t % kM;
-        const float v = F[k * kM + n];
-        float h, l;
-        tc::split_tf32(v, h, l);
-        img[t] = h;
-        img[kM * kM + t] = l;
-        mx = fmaxf(mx, fabsf(v));
-    }
+    for (int t = threadIdx.x; t < kM * kM; t += blockDim.x) mx = fmaxf(mx, fabsf(F[t]));
     for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -477,8 +786,8 @@ __global__ void k_gather_z32_rowmajor(const float* __restrict__ Vt, int ld, cons
 
 size_t tc32_workspace_bytes(int N) {
     const size_t K = (size_t)(N / kM);
-    // two sets of (W, S, F image (2 planes), max|F|), plus the sweep scratch
-    return 2 * (sizeof(float) * K * kM * kM * 4 + sizeof(float) * K + 1024) + sizeof(double) * 1100 + 4096;
+    // two sets of (W, F image (2 planes), max|F|), plus the sweep scratch
+    return 2 * (sizeof(float) * K * kM * kM * 3 + sizeof(float) * K + 1024) + sizeof(double) * 1100 + 4096;
 }
 
 namespace {
@@ -538,27 +847,26 @@ int gather_z32_rowmajor(const float* Vt, int ld, const int* perm, int n, double*
     return MPJ_SUCCESS;
 }
 
-int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol_abs,
-                         double eps_skip, int max_sweeps, int max_inner, void* work, cudaStream_t s,
-                         SweepResult* res) {
+int twosided_sweeps_tc32(float* T, float* Vt, int N, int n, double tol_abs, double eps_skip, int max_sweeps,
+                         int max_inner, void* work, cudaStream_t s, SweepResult* res) {
     if (N % kM != 0) { set_error_msg("tensor-core engine: N must be a multiple of 64"); return MPJ_BAD_ARG; }
     const int K = N / kM;
     Arena ar;
     ar.base = static_cast<char*>(work);
     ar.size = tc32_workspace_bytes(N);
     // Two sets of block-rotation buffers: the V pass of round g runs on a side
-    // stream (after the solve of round g), overlapping the next block solves.
-    float *Wbuf[2], *Sbuf[2], *Fimg[2], *fmax[2];
+    // stream (after the tile pass of round g), overlapping the next block solves.
+    float *Wbuf[2], *Fimg[2], *fmax[2];
     for (int set = 0; set < 2; ++set) {
         Wbuf[set] = ar.take<float>((size_t)K * kM * kM);
-        Sbuf[set] = ar.take<float>((size_t)K * kM * kM);
-        Fimg[set] = ar.take<float>((size_t)K * 2 * kM * kM);
+        Fimg[set] = ar.take<float>((size_t)K * kFImage);
         fmax[set] = ar.take<float>((size_t)K);
     }
     double* partial = ar.take<double>(1024);
     double* offv = ar.take<double>(4);
-    unsigned long long* rot = ar.take<unsigned long long>(4);     // [0] rotations, [1] error flag
-    if (!Wbuf[1] || !Sbuf[1] || !Fimg[1] || !fmax[1] || !partial || !offv || !rot) {
+    // [0] rotations, [1] error flag, [2] tiles updated by the tile pass
+    unsigned long long* rot = ar.take<unsigned long long>(4);
+    if (!Wbuf[1] || !Fimg[1] || !fmax[1] || !partial || !offv || !rot) {
         set_error_msg("workspace too small");
         return MPJ_BAD_ARG;
     }
@@ -567,18 +875,16 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_solve2_nb, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)InnerLayout<float, kM>::bytes));
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
-    PassMaps maps1[2], maps2[2];                         // per buffer set: pass 1, pass 2 and V
-    for (int set = 0; set < 2; ++set) {
-        MPJ_TRY(encode_rows(&maps1[set].in_t, T, N, N, kSlab));
-        MPJ_TRY(encode_rows(&maps1[set].v, Vt, N, N, kSlab));
-        MPJ_TRY(encode_rows(&maps1[set].f, Fimg[set], kM, (uint64_t)K * 2 * kM, kM));
-        maps2[set] = maps1[set];
-        MPJ_TRY(encode_rows(&maps2[set].in_t, P, N, N, kSlab));
-    }
+    const size_t tile_smem = tile_smem_bytes(K);
+    MPJ_CUDA_TRY(cudaFuncSetAttribute(k_tile_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem));
+    TileMaps tmaps;                                      // the tile pass: T in boxes of 32 x 32
+    PassMaps vmaps;                                      // the V pass: slabs of V
+    MPJ_TRY(encode_rows(&tmaps.t, T, N, N, kB));
+    MPJ_TRY(encode_rows(&vmaps.x, Vt, N, N, kSlab));
     SideStream side;
     MPJ_TRY(side.init(s));
     s = side.main;                                       // high priority: the critical path
-    MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, 2 * sizeof(unsigned long long), s));
+    MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, 3 * sizeof(unsigned long long), s));
     MPJ_TRY(offnorm2(T, false, N, n, partial, offv, s));
     MPJ_CUDA_TRY(cudaMemcpyAsync(hs.d, offv, sizeof(double), cudaMemcpyDeviceToHost, s));
     MPJ_CUDA_TRY(cudaStreamSynchronize(s));
@@ -590,53 +896,45 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
     const int rounds = 2 * K - 1;
     const int n_slabs = (N + kSlab - 1) / kSlab;
     const int items = n_slabs * K;
-    const int grid1 = items < 2 * sm_count() ? items : 2 * sm_count();
-    const int gridv = N >= 8192 ? items : grid1;
+    const int ntiles = K * (K - 1) / 2;
+    const int gridt = ntiles < 2 * sm_count() ? (ntiles > 0 ? ntiles : 1) : 2 * sm_count();
+    const int gridv = N >= 8192 ? items : (items < 2 * sm_count() ? items : 2 * sm_count());
     const float tau = (float)(tol_abs / (double)N);
     const float gate = 1.0f / 4096.0f;                   // Newton-Schulz when some |F| >= 2^-12
     // TF32 products per tile: 3 (about FP32 accuracy) or 1 (hi*hi only, about
     // 2^-11: a lower-precision step 1, mpj_options.stage1_tf32_terms)
     const int terms = knobs().stage1_terms;
     const int cross = N >= kB * kB ? cross_schedule(false, false) : 0;     // see cross_schedule
-    // the V pass joins after pass 2, so that it overlaps only the next round's
-    // block solves (measured at n = 4096: stage 1 238 -> 223 ms)
-    const bool v_late = true;
     while (res->sweeps < max_sweeps) {
         if (!std::isfinite(off)) { res->status = MPJ_NONFINITE_INPUT; break; }
         if (!(off > tol_abs)) { res->status = MPJ_SUCCESS; break; }
         MPJ_CUDA_TRY(cudaMemsetAsync(rot, 0, sizeof(unsigned long long), s));
+        MPJ_CUDA_TRY(cudaMemsetAsync(rot + 2, 0, sizeof(unsigned long long), s));
         for (int r = 0; r < rounds; ++r) {
             const int set = side.begin_round();
             if (set < 0) return MPJ_CUDA_ERROR;
             {
                 MPJ_PROF(PC_SOLVE2_F32, s);
                 k_solve2_nb<<<K, kSolve32Threads, InnerLayout<float, kM>::bytes, s>>>(
-                    T, N, Wbuf[set], Sbuf[set], Fimg[set], fmax[set], r, (float)eps_skip, tau, gate, max_inner,
-                    cross, rot);
+                    T, N, Wbuf[set], Fimg[set], fmax[set], r, (float)eps_skip, tau, gate, max_inner, cross, rot);
             }
             MPJ_LAUNCH_CHECK("k_solve2_nb");
-            if (!v_late) MPJ_TRY(side.after_solve());
-            {
-                MPJ_PROF(PC_TC1_F32, s);
-                k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps1[set], P, N, n_slabs, items, items, nullptr,
-                                                               fmax[set], r, terms, rot + 1);
+            if (ntiles > 0) {
+                MPJ_PROF(PC_TILE_F32, s);
+                k_tile_tc<<<gridt, kTcThreads, tile_smem, s>>>(tmaps, T, Fimg[set], N, ntiles, fmax[set], r, terms,
+                                                               rot + 1, rot + 2);
             }
-            MPJ_LAUNCH_CHECK("k_pass_tc pass 1");
-            {
-                MPJ_PROF(PC_TC2_F32, s);
-                k_pass_tc<<<grid1, kTcThreads, kPassSmem, s>>>(maps2[set], T, N, n_slabs, items, items, Sbuf[set],
-                                                               fmax[set], r, terms, rot + 1);
-            }
-            MPJ_LAUNCH_CHECK("k_pass_tc pass 2");
-            if (v_late) MPJ_TRY(side.after_solve());
+            MPJ_LAUNCH_CHECK("k_tile_tc");
+            // the V pass joins after the tile pass, so that it overlaps only the
+            // next round's block solves
+            MPJ_TRY(side.after_solve());
             {
                 // Persistent (two CTAs per SM) while a CTA has few tiles; one tile per CTA
                 // for N >= 8192, where the SM slots then free up tile by tile for the next
-                // block solve on the high-priority stream (measured: 273 vs 284 ms of
-                // step 1 at n = 4096, 1443 vs 1352 ms at n = 8192).
+                // block solve on the high-priority stream.
                 MPJ_PROF(PC_TCV_F32, side.sv);
-                k_pass_tc<<<gridv, kTcThreads, kPassSmem, side.sv>>>(maps2[set], T, N, n_slabs, 0, items, nullptr,
-                                                                     fmax[set], r, terms, rot + 1);
+                k_pass_tc<<<gridv, kTcThreads, kPassSmem, side.sv>>>(vmaps, Fimg[set], N, n_slabs, items, fmax[set],
+                                                                     r, terms, rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc V");
             MPJ_TRY(side.after_v());
@@ -644,16 +942,19 @@ int twosided_sweeps_tc32(float* T, float* Vt, float* P, int N, int n, double tol
         }
         MPJ_TRY(offnorm2(T, false, N, n, partial, offv, s));
         MPJ_CUDA_TRY(cudaMemcpyAsync(hs.d, offv, sizeof(double), cudaMemcpyDeviceToHost, s));
-        MPJ_CUDA_TRY(cudaMemcpyAsync(hs.u, rot, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+        MPJ_CUDA_TRY(cudaMemcpyAsync(hs.u, rot, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
         MPJ_CUDA_TRY(cudaStreamSynchronize(s));
         prof_flush();
         if (hs.u[1]) { set_error_msg("tensor-core tile: MMA completion wait timed out"); return MPJ_CUDA_ERROR; }
+        // algorithmic bytes of the tile pass: each updated tile is read once and
+        // written twice (64 x 64 FP32 each)
+        prof_add_units(PC_TILE_F32, (double)hs.u[2] * 3.0 * sizeof(float) * kM * kM);
         off = sqrt(hs.d[0]);
         res->sweeps += 1;
         res->rotations += (double)hs.u[0];
         if (trace_on())
-            fprintf(stderr, "[mpj] twosided<tc32> n=%d sweep %d: %llu rotations, off %.3e\n", n,
-                    res->sweeps, hs.u[0], off);
+            fprintf(stderr, "[mpj] twosided<tc32> n=%d sweep %d: %llu rotations, %llu tiles, off %.3e\n", n,
+                    res->sweeps, hs.u[0], hs.u[2], off);
         if (hs.u[0] == 0) { res->status = MPJ_SUCCESS; break; }
     }
     if (res->status == MPJ_NOT_CONVERGED && std::isfinite(off) && !(off > tol_abs))
@@ -707,7 +1008,7 @@ int onesided_sweeps_tc32(float* C, float* V, int m, int N, int n, double tol_rot
     float *Wbuf[2], *Fimg[2], *fmax[2];
     for (int set = 0; set < 2; ++set) {
         Wbuf[set] = ar.take<float>((size_t)K * kM * kM);
-        Fimg[set] = ar.take<float>((size_t)K * 2 * kM * kM);
+        Fimg[set] = ar.take<float>((size_t)K * kFImage);
         fmax[set] = ar.take<float>((size_t)K);
     }
     float* Ghi = ar.take<float>((size_t)K * nsplit * kM * kM);
@@ -721,15 +1022,9 @@ int onesided_sweeps_tc32(float* C, float* V, int m, int N, int n, double tol_rot
     MPJ_CUDA_TRY(cudaFuncSetAttribute(k_pass_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem));
     CUtensorMap mg;
     MPJ_TRY(encode_rows(&mg, C, N, m, 32));              // Gram: 32 rows x 32 columns per box
-    PassMaps mc[2], mv[2];                               // rotations: row slabs of C and of V
-    for (int set = 0; set < 2; ++set) {
-        MPJ_TRY(encode_rows(&mc[set].v, C, N, m, kSlab));
-        mc[set].in_t = mc[set].v;
-        MPJ_TRY(encode_rows(&mc[set].f, Fimg[set], kM, (uint64_t)K * 2 * kM, kM));
-        MPJ_TRY(encode_rows(&mv[set].v, V, N, N, kSlab));
-        mv[set].in_t = mv[set].v;
-        mv[set].f = mc[set].f;
-    }
+    PassMaps mc, mv;                                     // rotations: row slabs of C and of V
+    MPJ_TRY(encode_rows(&mc.x, C, N, m, kSlab));
+    MPJ_TRY(encode_rows(&mv.x, V, N, N, kSlab));
     SideStream side;
     MPJ_TRY(side.init(s));
     s = side.main;
@@ -763,15 +1058,15 @@ int onesided_sweeps_tc32(float* C, float* V, int m, int N, int n, double tol_rot
             MPJ_TRY(side.after_solve());
             {
                 MPJ_PROF(PC_APPLY1_F32, side.sv);
-                k_pass_tc<<<gridV, kTcThreads, kPassSmem, side.sv>>>(mv[set], nullptr, N, slabsV, 0, itemsV, nullptr,
-                                                                     fmax[set], r, 3, rot + 1);
+                k_pass_tc<<<gridV, kTcThreads, kPassSmem, side.sv>>>(mv, Fimg[set], N, slabsV, itemsV, fmax[set], r,
+                                                                     3, rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc V (one-sided)");
             MPJ_TRY(side.after_v());
             {
                 MPJ_PROF(PC_APPLY1_F32, s);
-                k_pass_tc<<<gridC, kTcThreads, kPassSmem, s>>>(mc[set], nullptr, N, slabsC, 0, itemsC, nullptr,
-                                                               fmax[set], r, 3, rot + 1);
+                k_pass_tc<<<gridC, kTcThreads, kPassSmem, s>>>(mc, Fimg[set], N, slabsC, itemsC, fmax[set], r, 3,
+                                                               rot + 1);
             }
             MPJ_LAUNCH_CHECK("k_pass_tc C (one-sided)");
             side.end_round();

@@ -240,9 +240,12 @@ def test_syevj_full_size_properties(mpj, n):
 
 
 # ------------------------------------------------------------------ SVD
-@pytest.mark.parametrize("m,n", [(48, 24), (200, 100), (300, 257)])
+@pytest.mark.parametrize("m,n", [(48, 24), (200, 100), (300, 257), (301, 257)])
 @pytest.mark.parametrize("method", ["mp", "plain"])
 def test_gesvj_parity(mpj, m, n, method):
+    """SVD against the oracle. n <= 256 runs the SIMT engines; 300 x 257 the
+    tensor-core FP32 step 1 and FP64 sweeps; 301 x 257 (odd m) the tensor-core step 1
+    and the SIMT FP64 sweeps (the FP64 tile maps need an even row count)."""
     A, sig, Uc, Vc = synth.svd_matrix(m, n, seed=synth.seed_for(2, n), sigma_min=1e-10)
     So, Uo, Vo, sto, rco = oracle.gesvj_plain(A)
     f = mpj.gesvj_mp if method == "mp" else mpj.gesvj_plain

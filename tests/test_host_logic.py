@@ -101,8 +101,10 @@ def test_alg_counts_closed_forms(n):
     assert c["apply2_f64"] == 2 * 3.0 * n ** 3
     Np = -(-n // 64) * 64
     assert realised["apply2_f64"] == 2 * 4.0 * Np ** 3
-    # one FP32 matrix read and written per pass and round
-    assert c["tc1_f32"] == 8.0 * Np * Np * (Np // 32 - 1) * 11
+    # one-pass tile update: the off-diagonal tiles (K (K - 1) / 2 of 64 x 64 FP32)
+    # read once and written twice per round
+    K = Np // 64
+    assert c["tile_f32"] == K * (K - 1) / 2 * 3 * 64 * 64 * 4 * (Np // 32 - 1) * 11
 
 
 def test_library_reads_no_environment():
