@@ -4,7 +4,8 @@
 //                   2K blocks are paired so that every pair meets once in 2K-1
 //                   rounds; pairs of one round are disjoint (the GPU analogue of
 //                   the "merry-go-round" order of Sec. 6).
-//   rotation_cs     Lemma 3.1 (and, on a Gram matrix, Lemma 5.1).
+//   rotation_cs_fast  Lemma 3.1 (and, on a Gram matrix, Lemma 5.1) in FP64 and
+//                   in FP32, with reciprocals and inverse square roots.
 //   inner_jacobi    cyclic Jacobi on one 2b x 2b block-pair problem held in
 //                   shared memory, parallel order inside the block, with the
 //                   rotations accumulated into the orthogonal 2b x 2b block W.
@@ -24,21 +25,10 @@ __device__ __forceinline__ int rr_index(int r, int pos, int P) {
     return pos == 0 ? 0 : 1 + (pos - 1 + r) % (P - 1);
 }
 
-// Lemma 3.1: (c, s) with mu = (a_qq - a_pp)/(2 a_pq), t = sign(mu)/(|mu| + sqrt(1+mu^2)),
-// c = 1/sqrt(1+t^2), s = t c.
-template <class Real>
-__device__ __forceinline__ void rotation_cs(Real app, Real aqq, Real apq, Real& c, Real& s, Real& t) {
-    Real mu = (aqq - app) / (Real(2) * apq);
-    Real am = mu < Real(0) ? -mu : mu;
-    t = Real(1) / (am + sqrt(Real(1) + mu * mu));
-    if (mu < Real(0)) t = -t;
-    c = Real(1) / sqrt(Real(1) + t * t);
-    s = t * c;
-}
-
 template <class Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
 
-// Lemma 3.1 in FP64 with reciprocals and reciprocal square roots in place of
+// Lemma 3.1: (c, s) with mu = (a_qq - a_pp)/(2 a_pq), t = sign(mu)/(|mu| + sqrt(1+mu^2)),
+// c = 1/sqrt(1+t^2), s = t c.  In FP64 with reciprocals and reciprocal square roots in place of
 // the divisions and square roots (a few ulps in t, c, s; the serial chain of a
 // step's rotations is a fraction as long, and on this GPU the block solves wait
 // on that chain).  For |mu| > 2^26, t = 1/(2 mu) to working precision.  Also
@@ -57,6 +47,31 @@ __device__ __forceinline__ void rotation_cs_fast(double app, double aqq, double 
     c = rsqrt(fma(t, t, 1.0));
     s = t * c;
     cm = -(s * s) * __drcp_rn(1.0 + c);
+}
+
+// Lemma 3.1 in FP32 the same way: the IEEE reciprocal and rsqrtf (2 ulp), whose
+// result takes one Newton step y <- y (3 - x y^2) / 2 for the inverse square
+// root, in place of the divisions and square roots, so that the serial chain of
+// a step's rotations is short.  For |mu| > 2^12, t = 1/(2 mu) to working
+// precision.  Also returns c - 1 = -s^2 / (1 + c) without cancellation.
+__device__ __forceinline__ float rsqrt_newton(float x) {
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+__device__ __forceinline__ void rotation_cs_fast(float app, float aqq, float apq, float& c, float& s, float& cm,
+                                                 float& t) {
+    const float mu = (aqq - app) * (0.5f * __frcp_rn(apq));
+    const float am = fabsf(mu);
+    if (am > 4096.0f) {
+        t = 0.5f * __frcp_rn(mu);
+    } else {
+        const float h = fmaf(mu, mu, 1.0f);
+        t = __frcp_rn(am + h * rsqrt_newton(h));
+        if (mu < 0.0f) t = -t;
+    }
+    c = rsqrt_newton(fmaf(t, t, 1.0f));
+    s = t * c;
+    cm = -(s * s) * __frcp_rn(1.0f + c);
 }
 
 // The rotation of a mixed-precision one-sided solve (Lemma 5.1 on a Gram
@@ -135,12 +150,7 @@ __device__ __forceinline__ int step_rotations(const Real* S, Real* cs, int* ip, 
         int skip = 1;
         Real aa = rabs(apq);
         if (apq != Real(0) && aa > tau && !(aa <= eps * sqrt(rabs(app * aqq)))) {
-            if constexpr (sizeof(Real) == 8) {
-                rotation_cs_fast(app, aqq, apq, c, s, cm, t);
-            } else {
-                rotation_cs(app, aqq, apq, c, s, t);
-                cm = -(s * s) / (Real(1) + c);
-            }
+            rotation_cs_fast(app, aqq, apq, c, s, cm, t);
             skip = 0;
         }
         cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = cm; cs[3 * P + tid] = t;
@@ -227,17 +237,22 @@ __device__ __forceinline__ void step_update_f(Real* F, const Real* cs, const int
     const int* iq = ip + P;
     const int* sk = ip + 2 * P;
     if constexpr (sizeof(Real) != 8) {
-        for (int t = t0; t < M * P; t += nt) {
-            int row = t % M, a = t / M;
+        // One warp per rotation (t0 and nt are whole warps): its parameters are
+        // loaded once, and the lanes take the rows.
+        const int lane = t0 & 31;
+        for (int a = t0 >> 5; a < P; a += nt >> 5) {
             if (sk[a]) continue;
-            int pa = ip[a], qa = iq[a];
-            Real c = cs[a], s = sn[a];
-            Real fp = F[pa * LD + row], fq = F[qa * LD + row];
-            Real np = c * fp - s * fq, nq = s * fp + c * fq;
-            if (row == pa) { np += cm[a]; nq += s; }
-            else if (row == qa) { np -= s; nq += cm[a]; }
-            F[pa * LD + row] = np;
-            F[qa * LD + row] = nq;
+            const int pa = ip[a], qa = iq[a];
+            const Real c = cs[a], s = sn[a], cma = cm[a];
+#pragma unroll
+            for (int row = lane; row < M; row += 32) {
+                const Real fp = F[pa * LD + row], fq = F[qa * LD + row];
+                Real np = c * fp - s * fq, nq = s * fp + c * fq;
+                if (row == pa) { np += cma; nq += s; }
+                else if (row == qa) { np -= s; nq += cma; }
+                F[pa * LD + row] = np;
+                F[qa * LD + row] = nq;
+            }
         }
         return;
     }
@@ -348,9 +363,19 @@ __device__ int inner_jacobi(Real* S, Real* F, Real* cs, int* ip, Real eps, Real 
             else if (nrows != M)
                 step_update_f_rows<Real, M>(F, csc, ipc, more ? tid - 32 : tid, more ? blockDim.x - 32 : blockDim.x,
                                             row0, nrows);
-            else if (more)
-                step_update_f<Real, M>(F, csc, ipc, tid - 32, blockDim.x - 32);
-            else
+            else if (more) {
+                if (sizeof(Real) == 4 && (blockDim.x & 127) == 0) {
+                    // FP32: the F work goes to the warps of the other three
+                    // sub-partitions (warp w runs on sub-partition w mod 4), so that
+                    // warp 0's chain of rotations has its sub-partition to itself
+                    const int w = tid >> 5;
+                    if (w & 3)
+                        step_update_f<Real, M>(F, csc, ipc, ((w >> 2) * 3 + (w & 3) - 1) * 32 + (tid & 31),
+                                               (int)(blockDim.x >> 7) * 96);
+                } else {
+                    step_update_f<Real, M>(F, csc, ipc, tid - 32, blockDim.x - 32);
+                }
+            } else
                 step_update_f<Real, M>(F, csc, ipc, tid, blockDim.x);
             __syncthreads();
         }
