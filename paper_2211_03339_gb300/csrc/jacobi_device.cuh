@@ -4,8 +4,8 @@
 //                   2K blocks are paired so that every pair meets once in 2K-1
 //                   rounds; pairs of one round are disjoint (the GPU analogue of
 //                   the "merry-go-round" order of Sec. 6).
-//   rotation_cs_fast  Lemma 3.1 (and, on a Gram matrix, Lemma 5.1) in FP64 and
-//                   in FP32, with reciprocals and inverse square roots.
+//   rotation_cs     Lemma 3.1 (and, on a Gram matrix, Lemma 5.1); in FP64 with
+//                   reciprocals and inverse square roots (rotation_cs_fast).
 //   inner_jacobi    cyclic Jacobi on one 2b x 2b block-pair problem held in
 //                   shared memory, parallel order inside the block, with the
 //                   rotations accumulated into the orthogonal 2b x 2b block W.
@@ -28,7 +28,18 @@ __device__ __forceinline__ int rr_index(int r, int pos, int P) {
 template <class Real> __device__ __forceinline__ Real rabs(Real x) { return x < Real(0) ? -x : x; }
 
 // Lemma 3.1: (c, s) with mu = (a_qq - a_pp)/(2 a_pq), t = sign(mu)/(|mu| + sqrt(1+mu^2)),
-// c = 1/sqrt(1+t^2), s = t c.  In FP64 with reciprocals and reciprocal square roots in place of
+// c = 1/sqrt(1+t^2), s = t c (IEEE arithmetic; the FP32 solves use it as it stands).
+template <class Real>
+__device__ __forceinline__ void rotation_cs(Real app, Real aqq, Real apq, Real& c, Real& s, Real& t) {
+    Real mu = (aqq - app) / (Real(2) * apq);
+    Real am = mu < Real(0) ? -mu : mu;
+    t = Real(1) / (am + sqrt(Real(1) + mu * mu));
+    if (mu < Real(0)) t = -t;
+    c = Real(1) / sqrt(Real(1) + t * t);
+    s = t * c;
+}
+
+// Lemma 3.1 in FP64 with reciprocals and reciprocal square roots in place of
 // the divisions and square roots (a few ulps in t, c, s; the serial chain of a
 // step's rotations is a fraction as long, and on this GPU the block solves wait
 // on that chain).  For |mu| > 2^26, t = 1/(2 mu) to working precision.  Also
@@ -47,31 +58,6 @@ __device__ __forceinline__ void rotation_cs_fast(double app, double aqq, double 
     c = rsqrt(fma(t, t, 1.0));
     s = t * c;
     cm = -(s * s) * __drcp_rn(1.0 + c);
-}
-
-// Lemma 3.1 in FP32 the same way: the IEEE reciprocal and rsqrtf (2 ulp), whose
-// result takes one Newton step y <- y (3 - x y^2) / 2 for the inverse square
-// root, in place of the divisions and square roots, so that the serial chain of
-// a step's rotations is short.  For |mu| > 2^12, t = 1/(2 mu) to working
-// precision.  Also returns c - 1 = -s^2 / (1 + c) without cancellation.
-__device__ __forceinline__ float rsqrt_newton(float x) {
-    const float y = rsqrtf(x);
-    return y * fmaf(-0.5f * x * y, y, 1.5f);
-}
-__device__ __forceinline__ void rotation_cs_fast(float app, float aqq, float apq, float& c, float& s, float& cm,
-                                                 float& t) {
-    const float mu = (aqq - app) * (0.5f * __frcp_rn(apq));
-    const float am = fabsf(mu);
-    if (am > 4096.0f) {
-        t = 0.5f * __frcp_rn(mu);
-    } else {
-        const float h = fmaf(mu, mu, 1.0f);
-        t = __frcp_rn(am + h * rsqrt_newton(h));
-        if (mu < 0.0f) t = -t;
-    }
-    c = rsqrt_newton(fmaf(t, t, 1.0f));
-    s = t * c;
-    cm = -(s * s) * __frcp_rn(1.0f + c);
 }
 
 // The rotation of a mixed-precision one-sided solve (Lemma 5.1 on a Gram
@@ -150,7 +136,12 @@ __device__ __forceinline__ int step_rotations(const Real* S, Real* cs, int* ip, 
         int skip = 1;
         Real aa = rabs(apq);
         if (apq != Real(0) && aa > tau && !(aa <= eps * sqrt(rabs(app * aqq)))) {
-            rotation_cs_fast(app, aqq, apq, c, s, cm, t);
+            if constexpr (sizeof(Real) == 8) {
+                rotation_cs_fast(app, aqq, apq, c, s, cm, t);
+            } else {
+                rotation_cs(app, aqq, apq, c, s, t);
+                cm = -(s * s) / (Real(1) + c);
+            }
             skip = 0;
         }
         cs[tid] = c; cs[P + tid] = s; cs[2 * P + tid] = cm; cs[3 * P + tid] = t;
