@@ -84,3 +84,20 @@ def test_product_package_does_not_import_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "oracle.c" not in txt, f
+
+
+def test_profile_counters_host_only(lib):
+    """The diagnostics are host state: every class has a name, the counters read
+    zero after a reset, and an out-of-range class or a missing output is rejected.
+    The byte count of the FP32 tile pass is a class of its own."""
+    import paper_2211_03339_gb300 as m
+    lib.mpj_profile_reset()
+    names = [lib.mpj_profile_name(k).decode() for k in range(lib.mpj_profile_classes())]
+    assert len(set(names)) == len(names) and all(names)
+    assert "tile_f32" in names and "solve2_f32" in names
+    assert all(v == 0.0 for v in m.profile_units().values())
+    assert all(v == (0, 0.0) for v in m.profile_read().values())
+    v = ctypes.c_double(1.0)
+    assert lib.mpj_profile_units(lib.mpj_profile_classes(), ctypes.byref(v)) != 0
+    assert lib.mpj_profile_units(-1, ctypes.byref(v)) != 0
+    assert lib.mpj_profile_units(0, None) != 0
